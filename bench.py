@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark: list-mode MLEM event-iterations/s on the paper-scale workload.
+
+Workload (default): two strips at +-350 mm, 500 mm long, 1 mm pixels
+(700 x 500), sigma_z = 10 mm, sigma_dl = 42 mm, 3-sigma windows, the paper's
+six-ellipse phantom with a cold insert, 1e7 seeded events, 20 iterations.  One
+step is one full reconstruction: reset the image and apply the 20 MLEM
+iterations (tsp_iterate, replayed from a CUDA graph) with the events resident
+in HBM.  value = events x iterations x steps / time of the timed steps.
+
+Also reported: the same metric end to end through the C ABI with host buffers
+(e2e: pinned-host event upload, per-event preparation and binning, the
+iterations and the image readout, every step), the dominant kernel's achieved
+pixel-evaluation rate against the SFU (MUFU) roofline, and the FP64 CPU oracle
+timed on the host's cores on a bounded sample of the same workload.
+
+``--impl reference`` times the FP64 CPU oracle instead (the reference arm).
+Multi-GPU (torchrun, one rank per GPU): each rank reconstructs its own
+independent event set (a different seed); no collective touches the data
+path; value is the sum over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLEM event-iterations/s (1e7 events, 1 mm grid), batched vs plain, rel err <=1e-4"
+UNIT = "event-iterations/s"
+MUFU_PER_PIXEL = 2          # one rsqrt and one ex2 per in-window pixel (pass 1)
+MUFU_PER_SM_CLK = 16        # SFU results per SM per clock (sm_100-class)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(workload, target_s: float = 12.0):
+    """Time the FP64 oracle (all host cores, as it stands) on a bounded sample:
+    one MLEM iteration over the first n events of the workload, n sized for
+    about target_s seconds.  Returns the baseline dict."""
+    import oracle
+    from oracle import Setup
+    st = Setup.from_workload(workload)
+    s = oracle.sensitivity(st)
+    w_small = _replace(workload, n_events=2000)
+    ev = w_small.events()
+    t0 = time.perf_counter()
+    oracle.mlem(st, ev, 1, s=s)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    n = int(min(workload.n_events, max(2000, 2000 * target_s / dt)))
+    ev = _replace(workload, n_events=n).events()
+    t0 = time.perf_counter()
+    oracle.mlem(st, ev, 1, s=s)
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"1 iteration of Eq. iter over the first {n} events of the "
+                      f"{workload.name} workload ({workload.ny}x{workload.nz} grid), FP64, "
+                      f"{dt:.1f} s"}
+
+
+def _replace(w, **kw):
+    from dataclasses import replace
+    return replace(w, **kw)
+
+
+def run_reference(args, workload):
+    """The reference arm: the FP64 CPU oracle, timed as it stands."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    from oracle import Setup
+    st = Setup.from_workload(workload)
+    s = oracle.sensitivity(st)
+    # size one step (one iteration over a sample) so the whole run takes ~minutes
+    probe = _replace(workload, n_events=2000).events()
+    t0 = time.perf_counter()
+    oracle.mlem(st, probe, 1, s=s)
+    per_event = (time.perf_counter() - t0) / 2000
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    n = int(min(workload.n_events, max(2000, budget / per_event)))
+    ev = _replace(workload, n_events=n).events()
+    rho = None
+    for _ in range(args.warmup):
+        rho, _ = oracle.mlem(st, ev, 1, rho0=rho, s=s)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rho, _ = oracle.mlem(st, ev, 1, rho0=rho, s=s)
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded phantom events)",
+        "config": {"workload": workload.name, "events": workload.n_events, "grid": [workload.ny, workload.nz],
+                   "pixel_mm": workload.dz, "sigma_z": workload.sigma_z, "sigma_dl": workload.sigma_dl,
+                   "cut": workload.cut, "step": f"1 MLEM iteration over a {n}-event sample"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} events of {workload.name}, 1 iteration per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tsp", choices=["tsp", "reference"])
+    ap.add_argument("--workload", default="paper_1mm")
+    ap.add_argument("--n-events", type=int, default=None, help="override the event count")
+    ap.add_argument("--iters", type=int, default=None, help="override iterations per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    from synth import make_workload
+    ws, rank, local = _dist()
+    over = {}
+    if args.n_events:
+        over["n_events"] = args.n_events
+    if args.iters:
+        over["n_iter"] = args.iters
+    workload = make_workload(args.workload, **over)
+    if args.impl == "reference":
+        return run_reference(args, workload)
+
+    import torch
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    if rank != 0 or ws > 1:
+        workload = _replace(workload, seed=workload.seed + 1000 * rank)
+
+    from paper_1502_07478_gb300 import Recon
+    ev = workload.events()
+    n_iter = workload.n_iter
+    n = workload.n_events
+    # pinned host copies for the end-to-end leg
+    pinned = [torch.from_numpy(e).pin_memory() for e in ev]
+    r = Recon.from_workload(workload)
+    r.upload_events(*ev)
+    r.set_profiling(True)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        r.set_image(None)
+        r.iterate(n_iter)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    st0 = r.stats()
+    if pg:
+        pg.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    pass_ms = r.pass_times()
+    st1 = r.stats()
+    launches = st1["launches"] - st0["launches"]
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    sec = ms / 1e3
+    value = ws * n * n_iter * args.steps / sec
+
+    # parity check at the benchmark's own size and launch configuration:
+    # count conservation sum_l s_l rho_l = N_used after the last iteration
+    s_map = r.compute_sensitivity().double()
+    rho = r.read_image().double()
+    cons = float((s_map * rho).sum()) / max(1, st1["n_used"]) - 1.0
+
+    # dominant kernel: the MLEM tile kernel; algorithmic work = in-window pixel
+    # evaluations per launch (exact count from the event preparation)
+    W = st1["n_window"]
+    t_pass = float(np.mean(pass_ms)) / 1e3 if pass_ms else float("nan")
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    peaks = _peaks()
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak = sms * f_max * MUFU_PER_SM_CLK / MUFU_PER_PIXEL
+    achieved = W / t_pass if pass_ms else None
+    roofline = {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
+                "peak": peak / 1e9, "unit": "Gpixel-evals/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "kernel": "k_tiles (MLEM pass, per launch)", "pixel_evals_per_launch": W,
+                "launch_ms": t_pass * 1e3,
+                "peak_basis": f"{sms} SMs x {f_max/1e6:.0f} MHz x {MUFU_PER_SM_CLK} SFU ops/clk"
+                              f" / {MUFU_PER_PIXEL} SFU ops per pixel evaluation"}
+
+    e2e = None
+    if not args.no_e2e:
+        out = np.empty((workload.ny, workload.nz), np.float32)
+        pinned_out = torch.empty((workload.ny, workload.nz), dtype=torch.float32).pin_memory()
+        r.set_profiling(False)
+
+        def e2e_step():
+            r.upload_events(*pinned)
+            r.iterate(n_iter)
+            r.read_image(out=pinned_out.numpy())
+
+        e2e_step()
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        t0 = time.perf_counter()
+        k_e2e = max(1, min(args.steps, 3))
+        for _ in range(k_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([dt], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": ws * n * n_iter * k_e2e / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(p.numel() * 4 for p in pinned)),
+               "d2h_bytes_per_step": int(pinned_out.numel() * 4), "steps": k_e2e}
+
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline(workload)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded phantom events; the paper's event sets are not published)",
+        "config": {"workload": workload.name, "events": n, "iterations_per_step": n_iter,
+                   "grid": [workload.ny, workload.nz], "pixel_mm": workload.dz,
+                   "sigma_z": workload.sigma_z, "sigma_dl": workload.sigma_dl,
+                   "cut": workload.cut, "form": "plain",
+                   "l2": "inputs larger than L2 (prepared events 24 B x 1e7 = 240 MB)",
+                   "parallelism": f"{ws} independent reconstructions" if ws > 1 else "1 GPU"},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "clocks": clk,
+        "checks": {"conservation_rel": cons, "n_used": st1["n_used"],
+                   "n_outliers": st1["n_outliers"], "n_empty": st1["n_empty"]},
+    }
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

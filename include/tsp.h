@@ -1,0 +1,159 @@
+/*
+ * tsp.h -- C ABI of libtsp, a GB300 (sm_103a) implementation of list-mode MLEM
+ * reconstruction for the two-strip time-of-flight PET detector of
+ * Bialas et al., "GPU accelerated image reconstruction in a two-strip J-PET
+ * tomograph" (arXiv:1502.07478).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Units are millimetres.  The strips lie at y = +R (upper) and y = -R
+ *    (lower) along z in [-L/2, L/2] (Sec. 2, Fig. 1).
+ *  - Image layout: ny x nz float32, row-major, z contiguous; pixel (iy, iz) is
+ *    centred at y = -R + (iy + 1/2) dy, z = -L/2 + (iz + 1/2) dz.
+ *  - Events are three float32 arrays of length n (structure of arrays): the
+ *    measured hit positions z_u, z_d along the upper and lower strip and the
+ *    path-length difference delta_l (Sec. 2, Eq. 1).
+ *  - on_device = 1 means the pointer is device memory of the current CUDA
+ *    device (for example a torch tensor's data_ptr()); 0 means host memory.
+ *    Host pointers are only borrowed for the duration of the call; the library
+ *    copies what it keeps.  Device pointers given by the caller are never freed
+ *    by the library.
+ *  - stream is a cudaStream_t (NULL = legacy default stream).  Calls enqueue
+ *    work on it; calls that return host-side values synchronise it.
+ *  - Return value 0 = success; a negative TSP_E* code on failure, with a
+ *    message available from tsp_last_error().  No entry point aborts the
+ *    process.  After TSP_ECUDA the context should be destroyed.
+ *  - A context is not thread-safe: calls on one context must be serialised by
+ *    the caller.  Distinct contexts are independent.
+ *  - The library owns all device memory it allocates and frees it in
+ *    tsp_destroy().
+ */
+#ifndef TSP_H
+#define TSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TSP_OK 0
+#define TSP_EINVAL (-1)   /* bad argument: sizes, NULL pointers, non-finite events */
+#define TSP_ENOMEM (-2)   /* a device or pinned-host allocation failed */
+#define TSP_ECUDA (-3)    /* a CUDA call failed (message holds the CUDA error) */
+#define TSP_ETIMEOUT (-4) /* a bounded device-side wait gave up */
+#define TSP_ESTATE (-5)   /* call out of order, e.g. iterate before any upload */
+
+typedef struct tsp_ctx tsp_ctx;
+
+/* Geometry, grid and resolution of one reconstruction. */
+typedef struct {
+    double R;          /* half of the strip separation (mm); > 0 */
+    double L;          /* strip length (mm); > 0 */
+    int32_t ny, nz;    /* image rows (y) and columns (z); > 0 */
+    double dy, dz;     /* pixel pitch (mm); 0 selects 2R/ny and L/nz */
+    double sigma_z;    /* resolution of z_u, z_d (mm); > 0.  Sec. 3, C^-1 */
+    double sigma_dl;   /* resolution of delta_l (mm); > 0.  Sec. 3, C^-1 */
+    double cut;        /* window radius in units of sigma; 0 selects 3 (Sec. 3) */
+    int32_t flags;     /* reserved, must be 0 */
+    int32_t reserved;
+} tsp_params;
+
+/* Counters of the last upload / pass (filled by tsp_stats). */
+typedef struct {
+    int64_t n_events;    /* events uploaded */
+    int64_t n_used;      /* events with a positive denominator in the last pass */
+    int64_t n_empty;     /* events whose window holds no pixel of the grid */
+    int64_t n_outliers;  /* events whose window exceeds their tile's halo */
+    int64_t n_window;    /* in-window pixels summed over events (pixel evaluations
+                            per iteration), counted at upload */
+    int64_t iterations;  /* MLEM iterations applied since the last set_image */
+    int64_t launches;    /* kernel launches enqueued by this context so far
+                            (each replayed graph node counts once) */
+    int64_t n_qbad;      /* in-window pixels of the last pass with Q <= 0 (P = 0) */
+    int64_t n_clipped;   /* window pixels outside the staged tile region in the
+                            last pass (always 0 unless the library is faulty) */
+    double sum_s_rho;    /* sum_l s_l rho_l of the current image */
+} tsp_stats_t;
+
+/* Create a context for one reconstruction.  Validates params (TSP_EINVAL) and
+ * allocates the image-sized device buffers.  The sensitivity map is computed
+ * on first use.  *out receives the context; NULL on failure. */
+int tsp_create(const tsp_params* params, tsp_ctx** out);
+
+/* Free every resource of the context (NULL is accepted). */
+void tsp_destroy(tsp_ctx* ctx);
+
+/* Message of the last failure on ctx (or of the last failed tsp_create when
+ * ctx is NULL).  The string lives until the next call on the same context. */
+const char* tsp_last_error(const tsp_ctx* ctx);
+
+/* Library version string, e.g. "tsp 0.1 sm_103a". */
+const char* tsp_version(void);
+
+/* Upload n events (replacing any previous set) and prepare them for
+ * iteration: for each event the direct reconstruction of Eq. 2 (Sec. 2), the
+ * 3-sigma window's bounding box of App. B, and the binning of events by the
+ * image tile holding their window centre.  zu, zd, dl: n floats each, host or
+ * device (on_device).  n = 0 is valid (an empty list).  Non-finite values give
+ * TSP_EINVAL and upload nothing.  The image is reset to rho = 1. */
+int tsp_upload_events(tsp_ctx* ctx, const float* zu, const float* zd, const float* dl,
+                      int64_t n, int on_device, void* stream);
+
+/* Sensitivity map s(y, z) of Eq. s-yz at the pixel centres (clamped at 0).
+ * out (nullable) receives ny*nz floats, host or device (on_device). */
+int tsp_compute_sensitivity(tsp_ctx* ctx, float* out, int on_device, void* stream);
+
+/* Set the current image rho (ny*nz floats, host or device); rho = NULL sets
+ * the uniform image rho = 1.  Values must be finite and >= 0 (TSP_EINVAL is
+ * not checked on device data).  Resets the iteration counter. */
+int tsp_set_image(tsp_ctx* ctx, const float* rho, int on_device, void* stream);
+
+/* Apply n_iter >= 0 list-mode MLEM updates of Eq. iter (Sec. 2):
+ *   rho_l <- rho_l * sum_j P(e_j|l) / D_j,  D_j = sum_i P(e_j|i) s_i rho_i,
+ * with the kernel P of Eq. kernel (Sec. 3) over each event's 3-sigma window.
+ * Events with D_j = 0 are skipped.  The iterations are replayed from a CUDA
+ * graph captured on the first call with this n_iter.  Requires an upload
+ * (TSP_ESTATE otherwise).  Asynchronous on stream. */
+int tsp_iterate(tsp_ctx* ctx, int n_iter, void* stream);
+
+/* Copy the current image to out (ny*nz floats, host or device).  which = 0:
+ * rho of Eq. iter; which = 1: rho' = s * rho of Eq. iter-p. */
+int tsp_read_image(tsp_ctx* ctx, float* out, int which, int on_device, void* stream);
+
+/* List-mode Poisson log-likelihood of the current image,
+ *   L = sum_j log D_j - sum_i s_i rho_i  (events with D_j = 0 skipped),
+ * whose EM step is Eq. iter.  *out receives L (host double).  Synchronises. */
+int tsp_loglik(tsp_ctx* ctx, double* out, void* stream);
+
+/* L and its gradient at the current image and resolution, with windows fixed
+ * at the current sigmas:
+ *   g_rho[l]   = s_l (sum_j P_jl / D_j - 1)                    (ny*nz floats)
+ *   g_sigma[k] = sum_j (1/D_j) sum_i s_i rho_i dP_ji/dsigma_k, k = (z, dl)
+ * The denominators D_j are recomputed, not stored.  L_out, g_rho (host or
+ * device per g_on_device) and g_sigma (host, 2 doubles) are each nullable.
+ * Synchronises. */
+int tsp_loglik_grad(tsp_ctx* ctx, double* L_out, float* g_rho, int g_on_device,
+                    double* g_sigma, void* stream);
+
+/* Change the resolution (sigma_z, sigma_dl > 0) used by the kernel and the
+ * windows.  The uploaded events are re-prepared (windows and binning depend on
+ * sigma); the image is kept. */
+int tsp_set_sigma(tsp_ctx* ctx, double sigma_z, double sigma_dl, void* stream);
+
+/* Fill *out with the counters of the context (synchronises stream). */
+int tsp_stats(tsp_ctx* ctx, tsp_stats_t* out, void* stream);
+
+/* Profiling aid (no counterpart in the paper).  With on = 1, graphs captured
+ * from now on record a CUDA event pair around each launch of the main MLEM
+ * kernel; tsp_pass_times then returns the device durations (ms) of those
+ * launches in the last tsp_iterate call, in order.  *count receives the number
+ * written (at most max).  Synchronises stream. */
+int tsp_set_profiling(tsp_ctx* ctx, int on);
+int tsp_pass_times(tsp_ctx* ctx, float* ms, int max, int* count, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TSP_H */

@@ -1,0 +1,694 @@
+// libtsp host side: the C ABI declared in include/tsp.h.
+//
+// A context owns the image buffers (rho, rho' = s rho, the back-projection
+// accumulator A, the sensitivity s), the uploaded events and their prepared,
+// binned form, and a cache of CUDA graphs that replay n iterations of
+// Eq. iter.  Every entry point validates its arguments, runs on the context's
+// device, and reports failures through return codes and tsp_last_error().
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/tsp.h"
+#include "tsp_launch.h"
+
+using namespace tsp;
+
+struct tsp_ctx {
+    tsp_params p{};
+    Geo g{};
+    Tiling tl{};
+    int lmax = 0, nseg = 1, G = 1;
+    int dev = 0, num_sms = 0;
+    size_t smem = 0;
+    int npix = 0;
+    int nbins = 0;
+    float* rho = nullptr;
+    float* rhop = nullptr;   // s * rho, padded by kPadFloats zeros
+    float* A = nullptr;
+    float* s = nullptr;
+    float* gbuf = nullptr;
+    Accum* accum = nullptr;
+    long long n = 0, cap = 0;
+    float *zu = nullptr, *zd = nullptr, *dl = nullptr;
+    float4 *geo_u = nullptr, *geo = nullptr;
+    int2 *rows_u = nullptr, *rows = nullptr;
+    int* key = nullptr;
+    int4* items = nullptr;
+    int n_items = 0, items_cap = 0;
+    long long outlier_first = 0, n_outliers = 0;
+    unsigned long long counters_h[4] = {0, 0, 0, 0};
+    unsigned long long* counters = nullptr;
+    int* bin_count = nullptr;
+    long long* offsets = nullptr;
+    int* cursor = nullptr;
+    int* flag = nullptr;
+    bool uploaded = false, sens_ready = false;
+    long long iterations = 0;
+    cudaStream_t cap_stream = nullptr;
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        long long launches = 0;               // kernel nodes per replay
+        std::vector<cudaEvent_t> ev;          // start/stop pairs around each MLEM pass
+    };
+    std::map<int, Graph> graphs;
+    int last_graph = -1;                      // n_iter of the last replayed graph
+    bool profiling = false;
+    long long launches = 0;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int fail(tsp_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return code;
+}
+
+#define TSP_CUDA(ctx, call)                                                                   \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? TSP_ENOMEM : TSP_ECUDA,      \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    } while (0)
+
+template <class T>
+void dfree(T*& p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void clear_graphs(tsp_ctx* c)
+{
+    for (auto& kv : c->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        for (cudaEvent_t e : kv.second.ev) cudaEventDestroy(e);
+    }
+    c->graphs.clear();
+    c->last_graph = -1;
+}
+
+// Kernel launches made by one MLEM/loglik/gradient pass.
+long long pass_launches(const tsp_ctx* c)
+{
+    return (c->n_items > 0 ? 1 : 0) + (c->n_outliers > 0 ? 1 : 0);
+}
+
+// Derive the kernel constants, lane capacity, group size and tiling from the
+// parameters.  Returns TSP_OK or TSP_EINVAL.
+int plan(tsp_ctx* c)
+{
+    const tsp_params& p = c->p;
+    const double dy = p.dy > 0 ? p.dy : 2.0 * p.R / p.ny;
+    const double dz = p.dz > 0 ? p.dz : p.L / p.nz;
+    const double cut = p.cut > 0 ? p.cut : 3.0;
+    const double iz = 1.0 / (p.sigma_z * p.sigma_z), il = 1.0 / (p.sigma_dl * p.sigma_dl);
+    const double log2e = 1.4426950408889634;
+    const double pi = 3.14159265358979323846;
+    Geo& g = c->g;
+    g.ny = p.ny;
+    g.nz = p.nz;
+    g.dy = (float)dy;
+    g.dz = (float)dz;
+    g.inv_dy = (float)(1.0 / dy);
+    g.inv_dz = (float)(1.0 / dz);
+    g.y0 = (float)(-p.R + 0.5 * dy);
+    g.z0 = (float)(-0.5 * p.L + 0.5 * dz);
+    g.R = (float)p.R;
+    g.iz = (float)iz;
+    g.il = (float)il;
+    g.cut2 = (float)(cut * cut);
+    g.hy_coef = (float)(cut * p.sigma_dl / 2.0);
+    g.hz_a = (float)(cut * cut * p.sigma_z * p.sigma_z / 2.0);
+    g.hz_b = (float)(cut * cut * p.sigma_dl * p.sigma_dl / 4.0);
+    // reading R4: K = det^(1/2)(C^-1) / (2 pi^2), det(C^-1) = iz^2 il
+    g.log2K = (float)std::log2(iz * std::sqrt(il) / (2.0 * pi * pi));
+    g.ksu = (float)std::sqrt(log2e * iz);
+    g.kA = (float)std::sqrt(log2e / 2.0);
+    g.half_log2e = (float)(log2e / 2.0);
+    g.inv_sqrt_2iz = (float)(1.0 / std::sqrt(2.0 * iz));
+
+    // lane capacity: the longest chord of the ellipse is 2 cut sigma_z / sqrt(2)
+    const double umax = cut * p.sigma_z / std::sqrt(2.0);
+    const int need = (int)std::floor(2.0 * umax / dz) + 2;
+    int best_l = 0, best_s = 0;
+    for (int nseg = 1; nseg <= 4 && !best_l; ++nseg)
+        for (int k = 0; k < kLmaxCount; ++k)
+            if (kLmaxList[k] * nseg >= need) {
+                best_l = kLmaxList[k];
+                best_s = nseg;
+                break;
+            }
+    if (!best_l) return fail(c, TSP_EINVAL, "window chords too long for the compiled lane capacities");
+    c->lmax = best_l;
+    c->nseg = best_s;
+    // rows of a window: |Dy| <= cut sigma_dl cos / 2
+    const double hy = cut * p.sigma_dl / 2.0 * 1.00001;
+    const int maxrows = (int)std::floor(2.0 * hy / dy) + 2;
+    const int lanes = maxrows * c->nseg;
+    c->G = (lanes + 31) / 32;
+    if (c->G > kWarps) return fail(c, TSP_EINVAL, "window has more rows than one block can hold");
+
+    // tiling: halo holds every window whose centre lies in the tile, for
+    // |tan theta~| <= 1; wider windows go to the outlier path.
+    Tiling& tl = c->tl;
+    tl.HY = (int)std::ceil(hy / dy) + 1;
+    const double hz_cap = std::sqrt(cut * cut * p.sigma_z * p.sigma_z / 2.0 +
+                                    cut * cut * p.sigma_dl * p.sigma_dl * 0.5 / 4.0) * 1.00001;
+    tl.HZ = (int)std::ceil(hz_cap / dz) + 1;
+    int RS = 33;
+    while (RS - 2 * tl.HZ < std::min(16, p.nz)) RS += 32;
+    tl.RS = RS;
+    tl.RW = RS;
+    tl.TZ = RS - 2 * tl.HZ;
+    const size_t budget = 200 * 1024;
+    const size_t fixed = (size_t)(kPadFloats + kWarps * 6) * sizeof(float);
+    int rh_max = (int)((budget - fixed) / (2 * sizeof(float) * (size_t)RS));
+    tl.TY = std::min(64, rh_max - 2 * tl.HY);
+    if (tl.TY < 4) return fail(c, TSP_EINVAL, "window halo too large for shared memory");
+    tl.TY = std::min(tl.TY, std::max(p.ny, 4));
+    tl.RH = tl.TY + 2 * tl.HY;
+    tl.tiles_y = (p.ny + tl.TY - 1) / tl.TY;
+    tl.tiles_z = (p.nz + tl.TZ - 1) / tl.TZ;
+    c->smem = (size_t)(2 * tl.RH * tl.RS) * sizeof(float) + fixed;
+    c->nbins = tl.tiles_y * tl.tiles_z + 1;
+    for (int mode = 0; mode < 3; ++mode) {
+        cudaError_t e = prepare_pass(c->lmax, mode, c->smem);
+        if (e != cudaSuccess)
+            return fail(c, TSP_ECUDA, std::string("prepare_pass: ") + cudaGetErrorString(e));
+    }
+    return TSP_OK;
+}
+
+int validate(const tsp_params* p, tsp_ctx* c)
+{
+    if (!p) return fail(c, TSP_EINVAL, "params is NULL");
+    auto pos = [](double v) { return std::isfinite(v) && v > 0.0; };
+    if (!pos(p->R) || !pos(p->L)) return fail(c, TSP_EINVAL, "R and L must be finite and > 0");
+    if (p->ny <= 0 || p->nz <= 0 || (long long)p->ny * p->nz > (1ll << 30))
+        return fail(c, TSP_EINVAL, "ny, nz must be > 0 and ny*nz <= 2^30");
+    if (!(p->dy == 0.0 || pos(p->dy)) || !(p->dz == 0.0 || pos(p->dz)))
+        return fail(c, TSP_EINVAL, "dy, dz must be 0 or finite and > 0");
+    if (!pos(p->sigma_z) || !pos(p->sigma_dl))
+        return fail(c, TSP_EINVAL, "sigma_z and sigma_dl must be finite and > 0");
+    if (!(p->cut == 0.0 || pos(p->cut))) return fail(c, TSP_EINVAL, "cut must be 0 or > 0");
+    if (p->flags != 0) return fail(c, TSP_EINVAL, "flags must be 0");
+    return TSP_OK;
+}
+
+int ensure_sensitivity(tsp_ctx* c, cudaStream_t st)
+{
+    if (c->sens_ready) return TSP_OK;
+    const tsp_params& p = c->p;
+    TSP_CUDA(c, launch_sensitivity(p.R, p.L, p.ny, p.nz, (double)c->g.dy, (double)c->g.dz, c->s, st));
+    c->launches += 1;
+    c->sens_ready = true;
+    return TSP_OK;
+}
+
+// rho' = s rho and sum s rho (into accum->sum_rhop, after clearing the accumulators)
+int refresh_rhop(tsp_ctx* c, cudaStream_t st)
+{
+    TSP_CUDA(c, launch_begin(c->accum, st));
+    TSP_CUDA(c, launch_set_rhop(c->npix, c->rho, c->s, c->rhop, c->accum, st));
+    c->launches += 2;
+    return TSP_OK;
+}
+
+PassArgs pass_args(tsp_ctx* c)
+{
+    PassArgs a;
+    a.g = c->g;
+    a.tl = c->tl;
+    a.evs.geo = c->geo;
+    a.evs.rows = c->rows;
+    a.items = c->items;
+    a.n_items = c->n_items;
+    a.outlier_first = (int)c->outlier_first;
+    a.outlier_count = (int)c->n_outliers;
+    a.rhop = c->rhop;
+    a.A = c->A;
+    a.accum = c->accum;
+    a.G = c->G;
+    a.nseg = c->nseg;
+    a.grid = c->num_sms;
+    a.smem = c->smem;
+    return a;
+}
+
+// Prepare the uploaded raw events: Eq. 2, windows, binning, work items.
+int prepare_events(tsp_ctx* c, cudaStream_t st)
+{
+    const long long n = c->n;
+    const int nbins = c->nbins;
+    dfree(c->bin_count);
+    dfree(c->offsets);
+    dfree(c->cursor);
+    TSP_CUDA(c, cudaMalloc(&c->bin_count, sizeof(int) * nbins));
+    TSP_CUDA(c, cudaMalloc(&c->offsets, sizeof(long long) * nbins));
+    TSP_CUDA(c, cudaMalloc(&c->cursor, sizeof(int) * nbins));
+    TSP_CUDA(c, cudaMemsetAsync(c->bin_count, 0, sizeof(int) * nbins, st));
+    TSP_CUDA(c, cudaMemsetAsync(c->cursor, 0, sizeof(int) * nbins, st));
+    TSP_CUDA(c, cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * 4, st));
+    TSP_CUDA(c, launch_setup(c->g, c->tl, n, c->zu, c->zd, c->dl, c->geo_u, c->rows_u, c->key,
+                             c->counters, c->bin_count, nbins, st));
+    c->launches += n > 0 ? 1 : 0;
+    std::vector<int> cnt(nbins);
+    TSP_CUDA(c, cudaMemcpyAsync(c->counters_h, c->counters, sizeof(c->counters_h),
+                                cudaMemcpyDeviceToHost, st));
+    TSP_CUDA(c, cudaMemcpyAsync(cnt.data(), c->bin_count, sizeof(int) * nbins,
+                                cudaMemcpyDeviceToHost, st));
+    TSP_CUDA(c, cudaStreamSynchronize(st));
+    if (c->counters_h[0] != 0) {
+        c->uploaded = false;
+        c->n = 0;
+        return fail(c, TSP_EINVAL, std::to_string(c->counters_h[0]) + " events are not finite");
+    }
+    std::vector<long long> off(nbins);
+    long long acc = 0;
+    for (int b = 0; b < nbins; ++b) {
+        off[b] = acc;
+        acc += cnt[b];
+    }
+    c->outlier_first = off[nbins - 1];
+    c->n_outliers = cnt[nbins - 1];
+    // work items: runs of at most E events of one tile, tiles interleaved
+    long long placed = acc - c->n_outliers;
+    long long E = placed / (8ll * std::max(1, c->num_sms));
+    E = std::max(32ll, std::min(4096ll, E));
+    std::vector<int4> items;
+    for (long long k = 0;; ++k) {
+        bool any = false;
+        for (int b = 0; b < nbins - 1; ++b) {
+            const long long first = k * E;
+            if (first < cnt[b]) {
+                any = true;
+                items.push_back(make_int4(b, (int)(off[b] + first),
+                                          (int)std::min<long long>(E, cnt[b] - first), 0));
+            }
+        }
+        if (!any) break;
+    }
+    if (acc > (1ll << 31) - 1) return fail(c, TSP_EINVAL, "more than 2^31-1 events");
+    c->n_items = (int)items.size();
+    if (c->n_items > c->items_cap) {
+        dfree(c->items);
+        TSP_CUDA(c, cudaMalloc(&c->items, sizeof(int4) * std::max(1, c->n_items)));
+        c->items_cap = c->n_items;
+    }
+    if (c->n_items)
+        TSP_CUDA(c, cudaMemcpyAsync(c->items, items.data(), sizeof(int4) * c->n_items,
+                                    cudaMemcpyHostToDevice, st));
+    TSP_CUDA(c, cudaMemcpyAsync(c->offsets, off.data(), sizeof(long long) * nbins,
+                                cudaMemcpyHostToDevice, st));
+    TSP_CUDA(c, launch_scatter(n, nbins, c->key, c->geo_u, c->rows_u, c->offsets, c->cursor, c->geo,
+                               c->rows, st));
+    c->launches += n > 0 ? 1 : 0;
+    clear_graphs(c);
+    c->uploaded = true;
+    return TSP_OK;
+}
+
+int ensure_event_capacity(tsp_ctx* c, long long n)
+{
+    if (n <= c->cap) return TSP_OK;
+    dfree(c->zu);
+    dfree(c->zd);
+    dfree(c->dl);
+    dfree(c->geo_u);
+    dfree(c->geo);
+    dfree(c->rows_u);
+    dfree(c->rows);
+    dfree(c->key);
+    c->cap = 0;
+    TSP_CUDA(c, cudaMalloc(&c->zu, sizeof(float) * n));
+    TSP_CUDA(c, cudaMalloc(&c->zd, sizeof(float) * n));
+    TSP_CUDA(c, cudaMalloc(&c->dl, sizeof(float) * n));
+    TSP_CUDA(c, cudaMalloc(&c->geo_u, sizeof(float4) * n));
+    TSP_CUDA(c, cudaMalloc(&c->geo, sizeof(float4) * n));
+    TSP_CUDA(c, cudaMalloc(&c->rows_u, sizeof(int2) * n));
+    TSP_CUDA(c, cudaMalloc(&c->rows, sizeof(int2) * n));
+    TSP_CUDA(c, cudaMalloc(&c->key, sizeof(int) * n));
+    c->cap = n;
+    return TSP_OK;
+}
+
+int capture_iterations(tsp_ctx* c, int n_iter, tsp_ctx::Graph* out)
+{
+    cudaStream_t cs = c->cap_stream;
+    cudaGraph_t graph = nullptr;
+    std::vector<cudaEvent_t> ev;
+    if (c->profiling) {
+        ev.resize(2 * (size_t)n_iter, nullptr);
+        for (auto& x : ev) TSP_CUDA(c, cudaEventCreate(&x));
+    }
+    TSP_CUDA(c, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    const PassArgs a = pass_args(c);
+    cudaError_t e = cudaSuccess;
+    for (int it = 0; it < n_iter && e == cudaSuccess; ++it) {
+        e = launch_begin(c->accum, cs);
+        if (e == cudaSuccess && c->profiling) e = cudaEventRecord(ev[2 * it], cs);
+        if (e == cudaSuccess) e = launch_pass(c->lmax, kMlem, a, cs);
+        if (e == cudaSuccess && c->profiling) e = cudaEventRecord(ev[2 * it + 1], cs);
+        if (e == cudaSuccess) e = launch_finalize(c->npix, c->rho, c->rhop, c->A, c->s, c->accum, cs);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return fail(c, TSP_ECUDA, std::string("graph capture: ") +
+                                      cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        for (cudaEvent_t x : ev) cudaEventDestroy(x);
+        return fail(c, TSP_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    out->exec = exec;
+    out->launches = (long long)n_iter * (2 + pass_launches(c));
+    out->ev = std::move(ev);
+    return TSP_OK;
+}
+
+int copy_floats(tsp_ctx* c, float* dst, const float* src, size_t n, int dst_dev, int src_dev,
+                cudaStream_t st)
+{
+    if (n == 0) return TSP_OK;
+    cudaMemcpyKind k = dst_dev ? (src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice)
+                               : (src_dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost);
+    TSP_CUDA(c, cudaMemcpyAsync(dst, src, n * sizeof(float), k, st));
+    return TSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tsp_version(void) { return "tsp 0.1 sm_103a"; }
+
+const char* tsp_last_error(const tsp_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+int tsp_create(const tsp_params* params, tsp_ctx** out)
+{
+    if (!out) return fail(nullptr, TSP_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate(params, nullptr);
+    if (rc) return rc;
+    tsp_ctx* c = new tsp_ctx();
+    c->p = *params;
+    auto bail = [&](int code) {
+        g_create_error = c->err;
+        tsp_destroy(c);
+        return code;
+    };
+    if (cudaGetDevice(&c->dev) != cudaSuccess) {
+        c->err = "no CUDA device";
+        return bail(TSP_ECUDA);
+    }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev);
+    if ((rc = plan(c))) return bail(rc);
+    c->npix = params->ny * params->nz;
+    const size_t img = sizeof(float) * (size_t)c->npix;
+    const size_t padded = img + sizeof(float) * kPadFloats;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&c->rho, img);
+    if (e == cudaSuccess) e = cudaMalloc(&c->rhop, padded);
+    if (e == cudaSuccess) e = cudaMalloc(&c->A, padded);
+    if (e == cudaSuccess) e = cudaMalloc(&c->s, img);
+    if (e == cudaSuccess) e = cudaMalloc(&c->gbuf, img);
+    if (e == cudaSuccess) e = cudaMalloc(&c->accum, sizeof(Accum));
+    if (e == cudaSuccess) e = cudaMalloc(&c->counters, sizeof(unsigned long long) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c->flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemset(c->rhop, 0, padded);
+    if (e == cudaSuccess) e = cudaMemset(c->A, 0, padded);
+    if (e == cudaSuccess) e = cudaMemset(c->accum, 0, sizeof(Accum));
+    if (e == cudaSuccess) e = launch_fill(c->rho, c->npix, 1.0f, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        c->err = std::string("tsp_create: ") + cudaGetErrorString(e);
+        return bail(e == cudaErrorMemoryAllocation ? TSP_ENOMEM : TSP_ECUDA);
+    }
+    *out = c;
+    return TSP_OK;
+}
+
+void tsp_destroy(tsp_ctx* c)
+{
+    if (!c) return;
+    DeviceGuard dg(c->dev);
+    cudaDeviceSynchronize();
+    clear_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    dfree(c->rho); dfree(c->rhop); dfree(c->A); dfree(c->s); dfree(c->gbuf);
+    dfree(c->accum); dfree(c->counters); dfree(c->flag);
+    dfree(c->zu); dfree(c->zd); dfree(c->dl);
+    dfree(c->geo_u); dfree(c->geo); dfree(c->rows_u); dfree(c->rows); dfree(c->key);
+    dfree(c->items); dfree(c->bin_count); dfree(c->offsets); dfree(c->cursor);
+    delete c;
+}
+
+int tsp_upload_events(tsp_ctx* c, const float* zu, const float* zd, const float* dl, int64_t n,
+                      int on_device, void* stream)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(c, TSP_EINVAL, "n < 0");
+    if (n > 0 && (!zu || !zd || !dl)) return fail(c, TSP_EINVAL, "event pointer is NULL");
+    if (n > (1ll << 31) - 1) return fail(c, TSP_EINVAL, "more than 2^31-1 events");
+    DeviceGuard dg(c->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    if ((rc = ensure_event_capacity(c, std::max<long long>(n, 1)))) return rc;
+    c->n = n;
+    if ((rc = copy_floats(c, c->zu, zu, n, 1, on_device, st))) return rc;
+    if ((rc = copy_floats(c, c->zd, zd, n, 1, on_device, st))) return rc;
+    if ((rc = copy_floats(c, c->dl, dl, n, 1, on_device, st))) return rc;
+    if ((rc = ensure_sensitivity(c, st))) return rc;
+    if ((rc = prepare_events(c, st))) return rc;
+    TSP_CUDA(c, launch_fill(c->rho, c->npix, 1.0f, st));
+    c->launches += 1;
+    if ((rc = refresh_rhop(c, st))) return rc;
+    c->iterations = 0;
+    return TSP_OK;
+}
+
+int tsp_compute_sensitivity(tsp_ctx* c, float* out, int on_device, void* stream)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    DeviceGuard dg(c->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_sensitivity(c, st);
+    if (rc) return rc;
+    if (out) {
+        if ((rc = copy_floats(c, out, c->s, c->npix, on_device, 1, st))) return rc;
+        if (!on_device) TSP_CUDA(c, cudaStreamSynchronize(st));
+    }
+    return TSP_OK;
+}
+
+int tsp_set_image(tsp_ctx* c, const float* rho, int on_device, void* stream)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    DeviceGuard dg(c->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_sensitivity(c, st);
+    if (rc) return rc;
+    if (rho) {
+        if ((rc = copy_floats(c, c->rho, rho, c->npix, 1, on_device, st))) return rc;
+        if (!on_device) {
+            TSP_CUDA(c, cudaMemsetAsync(c->flag, 0, sizeof(int), st));
+            TSP_CUDA(c, launch_check_image(c->npix, c->rho, c->flag, st));
+            c->launches += 1;
+            int bad = 0;
+            TSP_CUDA(c, cudaMemcpyAsync(&bad, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+            TSP_CUDA(c, cudaStreamSynchronize(st));
+            if (bad) {
+                launch_fill(c->rho, c->npix, 1.0f, st);
+                refresh_rhop(c, st);
+                return fail(c, TSP_EINVAL, "image values must be finite and >= 0");
+            }
+        }
+    } else {
+        TSP_CUDA(c, launch_fill(c->rho, c->npix, 1.0f, st));
+        c->launches += 1;
+    }
+    if ((rc = refresh_rhop(c, st))) return rc;
+    c->iterations = 0;
+    return TSP_OK;
+}
+
+int tsp_iterate(tsp_ctx* c, int n_iter, void* stream)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (n_iter < 0) return fail(c, TSP_EINVAL, "n_iter < 0");
+    if (!c->uploaded) return fail(c, TSP_ESTATE, "iterate before upload_events");
+    if (n_iter == 0) return TSP_OK;
+    DeviceGuard dg(c->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    auto it = c->graphs.find(n_iter);
+    if (it == c->graphs.end()) {
+        tsp_ctx::Graph gr;
+        int rc = capture_iterations(c, n_iter, &gr);
+        if (rc) return rc;
+        it = c->graphs.emplace(n_iter, std::move(gr)).first;
+    }
+    TSP_CUDA(c, cudaGraphLaunch(it->second.exec, st));
+    c->launches += it->second.launches;
+    c->last_graph = n_iter;
+    c->iterations += n_iter;
+    return TSP_OK;
+}
+
+int tsp_read_image(tsp_ctx* c, float* out, int which, int on_device, void* stream)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (!out) return fail(c, TSP_EINVAL, "out is NULL");
+    if (which != 0 && which != 1) return fail(c, TSP_EINVAL, "which must be 0 (rho) or 1 (rho')");
+    DeviceGuard dg(c->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = copy_floats(c, out, which ? c->rhop : c->rho, c->npix, on_device, 1, st);
+    if (rc) return rc;
+    if (!on_device) TSP_CUDA(c, cudaStreamSynchronize(st));
+    return TSP_OK;
+}
+
+int tsp_loglik(tsp_ctx* c, double* out, void* stream)
+{
+    return tsp_loglik_grad(c, out, nullptr, 0, nullptr, stream);
+}
+
+int tsp_loglik_grad(tsp_ctx* c, double* L_out, float* g_rho, int g_on_device, double* g_sigma,
+                    void* stream)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (!c->uploaded) return fail(c, TSP_ESTATE, "loglik before upload_events");
+    DeviceGuard dg(c->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = refresh_rhop(c, st);   // clears the accumulators, sums s rho
+    if (rc) return rc;
+    const bool grad = g_rho || g_sigma;
+    const PassArgs a = pass_args(c);
+    TSP_CUDA(c, launch_pass(c->lmax, grad ? kGrad : kLoglik, a, st));
+    c->launches += pass_launches(c);
+    if (grad) {
+        float* gdst = (g_rho && g_on_device) ? g_rho : c->gbuf;
+        TSP_CUDA(c, launch_grad_finalize(c->npix, gdst, c->A, c->s, st));
+        c->launches += 1;
+        if (g_rho && !g_on_device)
+            if ((rc = copy_floats(c, g_rho, c->gbuf, c->npix, 0, 1, st))) return rc;
+    }
+    Accum h;
+    TSP_CUDA(c, cudaMemcpyAsync(&h, c->accum, sizeof(Accum), cudaMemcpyDeviceToHost, st));
+    TSP_CUDA(c, cudaStreamSynchronize(st));
+    if (L_out) *L_out = h.sum_logD - h.sum_rhop;
+    if (g_sigma) {
+        const double sz = c->p.sigma_z, sl = c->p.sigma_dl;
+        g_sigma[0] = h.g_iz * (-2.0 / (sz * sz * sz));   // d iz / d sigma_z = -2 / sigma_z^3
+        g_sigma[1] = h.g_il * (-2.0 / (sl * sl * sl));
+    }
+    return TSP_OK;
+}
+
+int tsp_set_sigma(tsp_ctx* c, double sigma_z, double sigma_dl, void* stream)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (!(std::isfinite(sigma_z) && sigma_z > 0 && std::isfinite(sigma_dl) && sigma_dl > 0))
+        return fail(c, TSP_EINVAL, "sigmas must be finite and > 0");
+    DeviceGuard dg(c->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    tsp_params old = c->p;
+    c->p.sigma_z = sigma_z;
+    c->p.sigma_dl = sigma_dl;
+    int rc = plan(c);
+    if (rc) {
+        c->p = old;
+        plan(c);
+        return rc;
+    }
+    clear_graphs(c);
+    if (c->uploaded) {
+        if ((rc = prepare_events(c, st))) return rc;
+        if ((rc = refresh_rhop(c, st))) return rc;
+    }
+    return TSP_OK;
+}
+
+int tsp_stats(tsp_ctx* c, tsp_stats_t* out, void* stream)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (!out) return fail(c, TSP_EINVAL, "out is NULL");
+    DeviceGuard dg(c->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    Accum h;
+    TSP_CUDA(c, cudaMemcpyAsync(&h, c->accum, sizeof(Accum), cudaMemcpyDeviceToHost, st));
+    TSP_CUDA(c, cudaStreamSynchronize(st));
+    std::memset(out, 0, sizeof(*out));
+    out->n_events = c->n;
+    out->n_used = (int64_t)h.n_used;
+    out->n_empty = (int64_t)c->counters_h[1];
+    out->n_outliers = (int64_t)c->n_outliers;
+    out->n_window = (int64_t)c->counters_h[3];
+    out->iterations = c->iterations;
+    out->launches = c->launches;
+    out->n_qbad = (int64_t)h.n_qclip;
+    out->n_clipped = (int64_t)h.n_lclip;
+    out->sum_s_rho = h.sum_rhop;
+    return TSP_OK;
+}
+
+int tsp_set_profiling(tsp_ctx* c, int on)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    DeviceGuard dg(c->dev);
+    if ((bool)on != c->profiling) {
+        TSP_CUDA(c, cudaDeviceSynchronize());
+        clear_graphs(c);
+        c->profiling = on != 0;
+    }
+    return TSP_OK;
+}
+
+int tsp_pass_times(tsp_ctx* c, float* ms, int max, int* count, void* stream)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (!count || (max > 0 && !ms)) return fail(c, TSP_EINVAL, "NULL output");
+    *count = 0;
+    DeviceGuard dg(c->dev);
+    auto it = c->graphs.find(c->last_graph);
+    if (it == c->graphs.end() || it->second.ev.empty()) return TSP_OK;
+    TSP_CUDA(c, cudaStreamSynchronize((cudaStream_t)stream));
+    const auto& ev = it->second.ev;
+    int n = std::min<int>(max, (int)(ev.size() / 2));
+    for (int k = 0; k < n; ++k) TSP_CUDA(c, cudaEventElapsedTime(&ms[k], ev[2 * k], ev[2 * k + 1]));
+    *count = n;
+    return TSP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,173 @@
+// Device-side data structures and helpers shared by the libtsp kernels.
+//
+// Notation (Sec. 2-3 of the paper): an event is reconstructed by Eq. 2 at
+// (yt, zt) with tan(theta~) = t; c2i = 1 + t^2 = 1/cos^2(theta~).  For a pixel
+// centred at (y, z): Dy = y - yt, u = (z - zt) - t*Dy (the first two entries of
+// the vector b).  With the diagonal C^-1 = diag(iz, iz, il), iz = 1/sigma_z^2,
+// il = 1/sigma_dl^2, the quadratic forms of Eq. kernel reduce to
+//   bCb = 2 iz u^2 + 4 il Dy^2 c2i                               (App. B)
+//   aCa = 2 iz (R^2 + y^2) c2i^2 + 4 il y^2 t^2 c2i
+//   aCb = -2 iz y c2i u + 4 il y t Dy c2i
+//   oCb = -2 iz y t c2i u + 2 il y (1 + 2 t^2) Dy c2i
+// using a_3 = -2 y tan sec (the derivative of e_3 = -2 y sec).  Within one image
+// row (fixed y) every term is a polynomial of degree <= 2 in u, so each lane
+// computes row constants once and walks its chord of the 3-sigma ellipse.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tsp {
+
+constexpr int kThreads = 512;          // threads per persistent block (16 warps)
+constexpr int kWarps = kThreads / 32;
+constexpr int kPadFloats = 128;        // slack after image-sized buffers (>= max LMAX)
+
+enum Mode : int { kMlem = 0, kLoglik = 1, kGrad = 2 };
+
+// Per-reconstruction constants, passed by value to the kernels.
+struct Geo {
+    int ny, nz;
+    float y0, z0;           // centre of pixel (0, 0)
+    float dy, dz, inv_dy, inv_dz;
+    float R;
+    float iz, il;           // 1/sigma_z^2, 1/sigma_dl^2
+    float cut2;             // cut^2: window is bCb <= cut2
+    float hy_coef;          // bounding-box half-height = hy_coef / sqrt(c2i)
+    float hz_a, hz_b;       // bounding-box half-width = sqrt(hz_a + hz_b * t^2/c2i)
+    float log2K;            // log2 of det^(1/2)(C^-1) / (2 pi^2)
+    float ksu;              // sqrt(log2(e) iz)
+    float kA;               // sqrt(log2(e) / 2)
+    float half_log2e;       // log2(e) / 2
+    float inv_sqrt_2iz;     // 1 / sqrt(2 iz)
+};
+
+// Image tiling used by the shared-memory accumulation.  Region of tile
+// (ty, tz): rows [ty*TY - HY, +RH), columns [tz*TZ - HZ, +RW), stored with row
+// stride RS floats.
+struct Tiling {
+    int TY, TZ, HY, HZ;
+    int RH, RW, RS;
+    int tiles_y, tiles_z;
+};
+
+// Device-side accumulators of one pass.
+struct Accum {
+    unsigned long long n_used;   // events with D > 0
+    unsigned long long n_qclip;  // in-window pixels dropped because Q <= 0
+    unsigned long long n_lclip;  // chord pixels beyond the lane capacity (must stay 0)
+    unsigned long long pad0;
+    double sum_logD;             // sum_j log D_j
+    double g_iz;                 // sum_j (1/D_j) sum_i rho'_i P_ji dlogP/d(iz)
+    double g_il;                 // sum_j (1/D_j) sum_i rho'_i P_ji dlogP/d(il)
+    double sum_rhop;             // sum_i s_i rho_i
+    int queue;                   // persistent-kernel work counter
+    int pad1[3];
+};
+
+// Prepared events in binned order.
+struct EventsView {
+    const float4* __restrict__ geo;  // (yt, zt, t, c2i) per event
+    const int2* __restrict__ rows;   // (first row, row count) of the non-empty chords
+};
+
+// Key of an event in the binning: its tile index, the outlier bin (the last
+// bin), or kKeyEmpty for events whose window holds no pixel centre.
+constexpr int kKeyEmpty = -1;
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void named_barrier(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Eq. 2 (first forms) for one event; returns false for non-finite input.
+__device__ __forceinline__ bool direct_reconstruction(const Geo& g, float zu, float zd, float dl,
+                                                      float4& ev)
+{
+    if (!(isfinite(zu) && isfinite(zd) && isfinite(dl))) return false;
+    float t = (zu - zd) / (2.0f * g.R);
+    float c2i = fmaf(t, t, 1.0f);
+    float yt = -0.5f * dl / sqrtf(c2i);
+    float zt = fmaf(yt, t, 0.5f * (zu + zd));
+    ev = make_float4(yt, zt, t, c2i);
+    return true;
+}
+
+// Clamp a float index range [lo, hi] to [0, n-1] without overflow in the
+// float -> int conversion.  Returns the number of indices (>= 0).
+__device__ __forceinline__ int clamp_range(float flo, float fhi, int n, int& lo)
+{
+    flo = fminf(fmaxf(flo, 0.0f), (float)n);
+    fhi = fmaxf(fminf(fhi, (float)(n - 1)), -1.0f);
+    lo = (int)flo;
+    int hi = (int)fhi;
+    return hi >= lo ? hi - lo + 1 : 0;
+}
+
+// The chord of row iy inside the event's cut ellipse: pixel columns
+// [lo, lo + count) with bCb <= cut2 at their centres, clipped to the grid.
+// Also returns Dy, y and B0 = 4 il Dy^2 c2i, zc = zt + t Dy.
+struct Chord {
+    int lo, count;
+    float y, Dy, B0, zc;
+};
+
+// Explicitly rounded operations (never contracted into FMAs), so that the
+// event preparation and the MLEM passes derive bit-identical chords whatever
+// the surrounding code lets the compiler fuse.
+__device__ __forceinline__ Chord row_chord(const Geo& g, const float4& ev, int iy)
+{
+    Chord c;
+    c.y = __fmaf_rn((float)iy, g.dy, g.y0);
+    c.Dy = __fsub_rn(c.y, ev.x);
+    c.B0 = __fmul_rn(__fmul_rn(__fmul_rn(4.0f * g.il, c.Dy), c.Dy), ev.w);
+    c.zc = __fmaf_rn(ev.z, c.Dy, ev.y);
+    c.lo = 0;
+    c.count = 0;
+    const float rem = __fsub_rn(g.cut2, c.B0);
+    if (rem >= 0.0f) {
+        const float umax = __fmul_rn(__fsqrt_rn(rem), g.inv_sqrt_2iz);
+        const float flo = ceilf(__fmul_rn(__fsub_rn(__fsub_rn(c.zc, umax), g.z0), g.inv_dz));
+        const float fhi = floorf(__fmul_rn(__fsub_rn(__fadd_rn(c.zc, umax), g.z0), g.inv_dz));
+        c.count = clamp_range(flo, fhi, g.nz, c.lo);
+    }
+    return c;
+}
+
+// Bounding box of the event's window in pixel rows and columns, clipped to the
+// grid (App. B half-extents, widened by 1e-5 relative so that FP32 rounding
+// never drops a row whose chord is non-empty).
+__device__ __forceinline__ void event_bbox(const Geo& g, const float4& ev, int& iy_lo, int& nrows,
+                                           int& iz_lo, int& ncols)
+{
+    float hy = g.hy_coef * rsqrtf(ev.w) * 1.00001f;
+    float s2 = ev.z * ev.z / ev.w;
+    float hz = sqrtf(fmaf(g.hz_b, s2, g.hz_a)) * 1.00001f;
+    nrows = clamp_range(ceilf((ev.x - hy - g.y0) * g.inv_dy), floorf((ev.x + hy - g.y0) * g.inv_dy),
+                        g.ny, iy_lo);
+    ncols = clamp_range(ceilf((ev.y - hz - g.z0) * g.inv_dz), floorf((ev.y + hz - g.z0) * g.inv_dz),
+                        g.nz, iz_lo);
+}
+
+}  // namespace tsp

@@ -1,0 +1,373 @@
+// Auxiliary kernels of libtsp: sensitivity (Eq. s-yz), per-event preparation
+// (Eq. 2 and the App. B window), binning of events by image tile, the image
+// update that closes one iteration of Eq. iter, and small reductions.
+#include <climits>
+
+#include "tsp_launch.h"
+
+namespace tsp {
+
+namespace {
+
+constexpr int kAuxThreads = 256;
+
+inline int blocks_for(long long n, int per_block, int cap = 65535 * 8)
+{
+    long long b = (n + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+    // blockDim.x == kAuxThreads
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kAuxThreads / 32; ++w) t += sh[w];
+    __syncthreads();
+    return t;
+}
+
+// Eq. s-yz at pixel centres, in double precision, clamped at 0.
+__global__ void k_sensitivity(double R, double L, int ny, int nz, double dy, double dz, float* s)
+{
+    const long long npix = (long long)ny * nz;
+    const double hl = 0.5 * L;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int iy = (int)(i / nz), iz = (int)(i - (long long)iy * nz);
+        const double y = -R + (iy + 0.5) * dy;
+        const double z = -hl + (iz + 0.5) * dz;
+        double v = 0.0;
+        if (fabs(y) < R) {
+            const double tmax = fmin((hl - z) / (R - y), (hl + z) / (R + y));
+            const double tmin = fmax(-(hl + z) / (R - y), (z - hl) / (R + y));
+            v = (atan(tmax) - atan(tmin)) / 3.14159265358979323846;
+        }
+        s[i] = (float)fmax(v, 0.0);
+    }
+}
+
+// Per-event preparation.  counters: [0] non-finite events, [1] events with an
+// empty window, [2] outliers, [3] in-window pixels (pixel evaluations).
+// bin_count has nbins entries; the last bin collects the outliers.
+__global__ void k_setup(Geo g, Tiling tl, long long n, const float* __restrict__ zu,
+                        const float* __restrict__ zd, const float* __restrict__ dl,
+                        float4* __restrict__ geo, int2* __restrict__ rows, int* __restrict__ key,
+                        unsigned long long* counters, int* bin_count, int nbins)
+{
+    extern __shared__ int s_hist[];
+    const bool use_smem = nbins <= 8192;
+    if (use_smem) {
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x) s_hist[b] = 0;
+        __syncthreads();
+    }
+    unsigned long long bad = 0, empty = 0, outl = 0, pix = 0;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        float4 ev = make_float4(0.f, 0.f, 0.f, 1.f);
+        int k = kKeyEmpty;
+        int2 rw = make_int2(0, 0);
+        if (!direct_reconstruction(g, zu[j], zd[j], dl[j], ev)) {
+            ++bad;
+        } else {
+            int iy_lo, nrows, iz_lo, ncols;
+            event_bbox(g, ev, iy_lo, nrows, iz_lo, ncols);
+            int first = -1, last = -1, zmin = INT_MAX, zmax = -1;
+            unsigned long long cnt = 0;
+            for (int r = 0; r < nrows; ++r) {
+                const Chord c = row_chord(g, ev, iy_lo + r);
+                if (c.count > 0) {
+                    if (first < 0) first = iy_lo + r;
+                    last = iy_lo + r;
+                    cnt += (unsigned long long)c.count;
+                    zmin = min(zmin, c.lo);
+                    zmax = max(zmax, c.lo + c.count - 1);
+                }
+            }
+            if (cnt == 0) {
+                ++empty;
+            } else {
+                pix += cnt;
+                rw = make_int2(first, last - first + 1);
+                // tile of the pixel holding the window centre (clamped to the grid)
+                const float fy = fminf(fmaxf(floorf((ev.x - g.y0) * g.inv_dy + 0.5f), 0.f),
+                                       (float)(g.ny - 1));
+                const float fz = fminf(fmaxf(floorf((ev.y - g.z0) * g.inv_dz + 0.5f), 0.f),
+                                       (float)(g.nz - 1));
+                const int ty = (int)fy / tl.TY, tz = (int)fz / tl.TZ;
+                const int oy = ty * tl.TY - tl.HY, oz = tz * tl.TZ - tl.HZ;
+                const bool fits = first >= oy && last < oy + tl.RH && zmin >= oz && zmax < oz + tl.RW;
+                k = fits ? ty * tl.tiles_z + tz : nbins - 1;
+                if (!fits) ++outl;
+            }
+        }
+        geo[j] = ev;
+        rows[j] = rw;
+        key[j] = k;
+        if (k >= 0) {
+            if (use_smem) atomicAdd(&s_hist[k], 1);
+            else atomicAdd(&bin_count[k], 1);
+        }
+    }
+    // warp-aggregate the counters
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+        empty += __shfl_xor_sync(0xffffffffu, empty, o);
+        outl += __shfl_xor_sync(0xffffffffu, outl, o);
+        pix += __shfl_xor_sync(0xffffffffu, pix, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicAdd(&counters[0], bad);
+        if (empty) atomicAdd(&counters[1], empty);
+        if (outl) atomicAdd(&counters[2], outl);
+        if (pix) atomicAdd(&counters[3], pix);
+    }
+    if (use_smem) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+            if (s_hist[b]) atomicAdd(&bin_count[b], s_hist[b]);
+    }
+}
+
+// Counting-sort scatter of the prepared events into binned order.  Within a
+// block the rank of an event in its bin comes from a shared-memory counter and
+// one global reservation is made per (block, bin).
+__global__ void k_scatter(long long n, int nbins, const int* __restrict__ key,
+                          const float4* __restrict__ geo_in, const int2* __restrict__ rows_in,
+                          const long long* __restrict__ offsets, int* cursor,
+                          float4* __restrict__ geo_out, int2* __restrict__ rows_out)
+{
+    extern __shared__ int s_cnt[];   // [nbins] local counts, then [nbins] reserved bases
+    int* s_base = s_cnt + nbins;
+    const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) s_cnt[b] = 0;
+    __syncthreads();
+    int k = kKeyEmpty, rank = 0;
+    if (j < n) {
+        k = key[j];
+        if (k >= 0) rank = atomicAdd(&s_cnt[k], 1);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+        if (s_cnt[b]) s_base[b] = atomicAdd(&cursor[b], s_cnt[b]);
+    __syncthreads();
+    if (k >= 0) {
+        const long long pos = offsets[k] + s_base[k] + rank;
+        geo_out[pos] = geo_in[j];
+        rows_out[pos] = rows_in[j];
+    }
+}
+
+__global__ void k_scatter_global(long long n, const int* __restrict__ key,
+                                 const float4* __restrict__ geo_in, const int2* __restrict__ rows_in,
+                                 const long long* __restrict__ offsets, int* cursor,
+                                 float4* __restrict__ geo_out, int2* __restrict__ rows_out)
+{
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        const int k = key[j];
+        if (k < 0) continue;
+        const long long pos = offsets[k] + atomicAdd(&cursor[k], 1);
+        geo_out[pos] = geo_in[j];
+        rows_out[pos] = rows_in[j];
+    }
+}
+
+// Start of a pass: clear the accumulators and the work counter.
+__global__ void k_begin(Accum* a)
+{
+    if (threadIdx.x == 0) {
+        a->n_used = 0ull;
+        a->n_qclip = 0ull;
+        a->n_lclip = 0ull;
+        a->sum_logD = 0.0;
+        a->g_iz = 0.0;
+        a->g_il = 0.0;
+        a->sum_rhop = 0.0;
+        a->queue = 0;
+    }
+}
+
+// End of one iteration of Eq. iter: rho <- rho * A (A = sum_j P_j / D_j), then
+// rho' = s rho for the next pass, A <- 0, and sum_i s_i rho_i.
+__global__ void k_finalize(int npix, float* __restrict__ rho, float* __restrict__ rhop,
+                           float* __restrict__ A, const float* __restrict__ s, Accum* a)
+{
+    __shared__ double sh[kAuxThreads / 32];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += gridDim.x * blockDim.x) {
+        const float r = rho[i] * A[i];
+        const float p = s[i] * r;
+        rho[i] = r;
+        rhop[i] = p;
+        A[i] = 0.0f;
+        acc += (double)p;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) atomicAdd(&a->sum_rhop, acc);
+}
+
+// g_rho = s (A - 1); A <- 0.
+__global__ void k_grad_finalize(int npix, float* __restrict__ g, float* __restrict__ A,
+                                const float* __restrict__ s)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += gridDim.x * blockDim.x) {
+        g[i] = s[i] * (A[i] - 1.0f);
+        A[i] = 0.0f;
+    }
+}
+
+// rho' = s rho and sum_i rho'_i.
+__global__ void k_set_rhop(int npix, const float* __restrict__ rho, const float* __restrict__ s,
+                           float* __restrict__ rhop, Accum* a)
+{
+    __shared__ double sh[kAuxThreads / 32];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += gridDim.x * blockDim.x) {
+        const float p = s[i] * rho[i];
+        rhop[i] = p;
+        acc += (double)p;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) atomicAdd(&a->sum_rhop, acc);
+}
+
+__global__ void k_fill(float* p, long long n, float v)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+__global__ void k_product(int n, const float* __restrict__ a, const float* __restrict__ b,
+                          float* __restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = a[i] * b[i];
+}
+
+__global__ void k_check_image(int n, const float* __restrict__ rho, int* bad)
+{
+    int b = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float v = rho[i];
+        if (!(isfinite(v) && v >= 0.0f)) b = 1;
+    }
+    if (__any_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) atomicOr(bad, 1);
+}
+
+}  // namespace
+
+cudaError_t launch_sensitivity(double R, double L, int ny, int nz, double dy, double dz, float* s,
+                               cudaStream_t st)
+{
+    k_sensitivity<<<blocks_for((long long)ny * nz, kAuxThreads, 4096), kAuxThreads, 0, st>>>(
+        R, L, ny, nz, dy, dz, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup(const Geo& g, const Tiling& tl, long long n, const float* zu,
+                         const float* zd, const float* dl, float4* geo, int2* rows, int* key,
+                         unsigned long long* counters, int* bin_count, int nbins, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const size_t smem = nbins <= 8192 ? (size_t)nbins * sizeof(int) : 0;
+    k_setup<<<blocks_for(n, kAuxThreads * 8, 4096), kAuxThreads, smem, st>>>(
+        g, tl, n, zu, zd, dl, geo, rows, key, counters, bin_count, nbins);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(long long n, int nbins, const int* key, const float4* geo_in,
+                           const int2* rows_in, const long long* offsets, int* cursor,
+                           float4* geo_out, int2* rows_out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (nbins <= 4096) {
+        k_scatter<<<blocks_for(n, kAuxThreads * 4, INT_MAX), kAuxThreads * 4,
+                    2 * (size_t)nbins * sizeof(int), st>>>(n, nbins, key, geo_in, rows_in, offsets,
+                                                           cursor, geo_out, rows_out);
+    } else {
+        k_scatter_global<<<blocks_for(n, kAuxThreads, 4096), kAuxThreads, 0, st>>>(
+            n, key, geo_in, rows_in, offsets, cursor, geo_out, rows_out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_begin(Accum* accum, cudaStream_t st)
+{
+    k_begin<<<1, 32, 0, st>>>(accum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(int npix, float* rho, float* rhop, float* A, const float* s,
+                            Accum* accum, cudaStream_t st)
+{
+    k_finalize<<<blocks_for(npix, kAuxThreads * 4, 1024), kAuxThreads, 0, st>>>(npix, rho, rhop, A,
+                                                                               s, accum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_finalize(int npix, float* g, float* A, const float* s, cudaStream_t st)
+{
+    k_grad_finalize<<<blocks_for(npix, kAuxThreads * 4, 1024), kAuxThreads, 0, st>>>(npix, g, A, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_rhop(int npix, const float* rho, const float* s, float* rhop, Accum* accum,
+                            cudaStream_t st)
+{
+    k_set_rhop<<<blocks_for(npix, kAuxThreads * 4, 1024), kAuxThreads, 0, st>>>(npix, rho, s, rhop,
+                                                                               accum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    k_fill<<<blocks_for(n, kAuxThreads * 4, 4096), kAuxThreads, 0, st>>>(p, n, v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_product(int n, const float* a, const float* b, float* out, cudaStream_t st)
+{
+    k_product<<<blocks_for(n, kAuxThreads * 4, 1024), kAuxThreads, 0, st>>>(n, a, b, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_image(int n, const float* rho, int* bad, cudaStream_t st)
+{
+    k_check_image<<<blocks_for(n, kAuxThreads * 4, 1024), kAuxThreads, 0, st>>>(n, rho, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass(int lmax, int mode, const PassArgs& a, cudaStream_t st)
+{
+    switch (lmax) {
+    case 12: return launch_pass_l<12>(mode, a, st);
+    case 24: return launch_pass_l<24>(mode, a, st);
+    case 48: return launch_pass_l<48>(mode, a, st);
+    case 64: return launch_pass_l<64>(mode, a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t prepare_pass(int lmax, int mode, size_t smem)
+{
+    switch (lmax) {
+    case 12: return prepare_pass_l<12>(mode, smem);
+    case 24: return prepare_pass_l<24>(mode, smem);
+    case 48: return prepare_pass_l<48>(mode, smem);
+    case 64: return prepare_pass_l<64>(mode, smem);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace tsp

@@ -1,0 +1,59 @@
+// Host-side launch interface of the libtsp kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tsp_device.cuh"
+
+namespace tsp {
+
+// Lane capacities (pixels of one row segment held in registers) compiled in.
+constexpr int kLmaxList[] = {12, 24, 48, 64};
+constexpr int kLmaxCount = 4;
+
+struct PassArgs {
+    Geo g;
+    Tiling tl;
+    EventsView evs;
+    const int4* items;
+    int n_items;
+    int outlier_first, outlier_count;
+    const float* rhop;
+    float* A;
+    Accum* accum;
+    int G, nseg;
+    int grid;          // persistent blocks
+    size_t smem;       // dynamic shared memory of the tile kernel
+};
+
+// Tile kernel + outlier kernel of one pass (MODE = kMlem, kLoglik or kGrad).
+cudaError_t launch_pass(int lmax, int mode, const PassArgs& a, cudaStream_t st);
+// Raise the dynamic shared-memory limit of the tile kernel for (lmax, mode).
+cudaError_t prepare_pass(int lmax, int mode, size_t smem);
+
+// Per-LMAX entry points (one translation unit each).
+template <int LMAX>
+cudaError_t launch_pass_l(int mode, const PassArgs& a, cudaStream_t st);
+template <int LMAX>
+cudaError_t prepare_pass_l(int mode, size_t smem);
+
+// Auxiliary kernels (tsp_kernels.cu).
+cudaError_t launch_sensitivity(double R, double L, int ny, int nz, double dy, double dz, float* s,
+                               cudaStream_t st);
+cudaError_t launch_setup(const Geo& g, const Tiling& tl, long long n, const float* zu,
+                         const float* zd, const float* dl, float4* geo, int2* rows, int* key,
+                         unsigned long long* counters, int* nbins_count, int nbins, cudaStream_t st);
+cudaError_t launch_scatter(long long n, int nbins, const int* key, const float4* geo_in,
+                           const int2* rows_in, const long long* offsets, int* cursor,
+                           float4* geo_out, int2* rows_out, cudaStream_t st);
+cudaError_t launch_begin(Accum* accum, cudaStream_t st);
+cudaError_t launch_finalize(int npix, float* rho, float* rhop, float* A, const float* s,
+                            Accum* accum, cudaStream_t st);
+cudaError_t launch_grad_finalize(int npix, float* g, float* A, const float* s, cudaStream_t st);
+cudaError_t launch_set_rhop(int npix, const float* rho, const float* s, float* rhop, Accum* accum,
+                            cudaStream_t st);
+cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t st);
+cudaError_t launch_product(int npix, const float* a, const float* b, float* out, cudaStream_t st);
+cudaError_t launch_check_image(int npix, const float* rho, int* bad, cudaStream_t st);
+
+}  // namespace tsp

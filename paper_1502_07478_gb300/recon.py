@@ -1,0 +1,209 @@
+"""Python binding of libtsp: the same operations as include/tsp.h, with torch
+tensors (device memory, streams) or NumPy arrays (host memory) as arguments.
+
+Nothing here computes any part of the reconstruction; every call forwards to
+the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import _lib as L
+
+try:
+    import torch
+except ImportError:  # pragma: no cover
+    torch = None
+
+
+def _stream_handle(stream=None):
+    if torch is None or not torch.cuda.is_available():
+        return None
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _arg(x, dtype=np.float32):
+    """(pointer, on_device, keepalive) for a torch tensor or array-like."""
+    if torch is not None and isinstance(x, torch.Tensor):
+        if x.is_cuda:
+            if x.dtype != torch.float32 or not x.is_contiguous():
+                x = x.to(torch.float32).contiguous()
+            return C.c_void_p(x.data_ptr()), 1, x
+        x = x.detach().numpy()
+    a = np.ascontiguousarray(np.asarray(x, dtype=dtype))
+    return C.c_void_p(a.ctypes.data), 0, a
+
+
+class Recon:
+    """One reconstruction: geometry, grid, resolution, events and image.
+
+    Mirrors tsp_create / tsp_upload_events / tsp_compute_sensitivity /
+    tsp_set_image / tsp_iterate / tsp_read_image / tsp_loglik /
+    tsp_loglik_grad / tsp_set_sigma / tsp_stats."""
+
+    def __init__(self, R: float, L_: float, ny: int, nz: int, sigma_z: float, sigma_dl: float,
+                 cut: float = 3.0, dy: float = 0.0, dz: float = 0.0, device: Optional[int] = None):
+        self._lib = L.lib()
+        if torch is not None and torch.cuda.is_available():
+            if device is not None:
+                torch.cuda.set_device(device)
+            torch.cuda.init()
+        self.ny, self.nz = int(ny), int(nz)
+        self.params = L.Params(float(R), float(L_), self.ny, self.nz, float(dy), float(dz),
+                               float(sigma_z), float(sigma_dl), float(cut), 0, 0)
+        h = C.c_void_p()
+        rc = self._lib.tsp_create(C.byref(self.params), C.byref(h))
+        L.check(None, rc)
+        self._h = h
+        self.device = torch.cuda.current_device() if torch is not None and \
+            torch.cuda.is_available() else None
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        return cls(w.R, w.L, w.ny, w.nz, w.sigma_z, w.sigma_dl, w.cut, **kw)
+
+    # -- lifetime --------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.tsp_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _chk(self, rc):
+        L.check(self._h, rc)
+
+    # -- operations --------------------------------------------------------------
+    def upload_events(self, zu, zd, dl, stream=None):
+        pu, du, ku = _arg(zu)
+        pd, dd, kd = _arg(zd)
+        pl, dl_, kl = _arg(dl)
+        if not (du == dd == dl_):
+            raise ValueError("zu, zd, dl must all be host arrays or all be CUDA tensors")
+        n = int(ku.numel() if du else ku.size)
+        if (kd.numel() if dd else kd.size) != n or (kl.numel() if dl_ else kl.size) != n:
+            raise ValueError("zu, zd, dl must have the same length")
+        self._chk(self._lib.tsp_upload_events(self._h, pu, pd, pl, n, du, _stream_handle(stream)))
+
+    def compute_sensitivity(self, out=None, stream=None):
+        """Sensitivity map (Eq. s-yz) as a CUDA tensor (or into ``out``)."""
+        if out is None:
+            out = torch.empty(self.ny, self.nz, dtype=torch.float32, device="cuda")
+        p, dev, keep = _arg(out)
+        self._chk(self._lib.tsp_compute_sensitivity(self._h, p, dev, _stream_handle(stream)))
+        return out
+
+    def set_image(self, rho=None, stream=None):
+        if rho is None:
+            self._chk(self._lib.tsp_set_image(self._h, None, 0, _stream_handle(stream)))
+            return
+        p, dev, keep = _arg(rho)
+        size = keep.numel() if dev else keep.size
+        if size != self.ny * self.nz:
+            raise ValueError("image must have ny*nz elements")
+        self._chk(self._lib.tsp_set_image(self._h, p, dev, _stream_handle(stream)))
+
+    def iterate(self, n_iter: int, stream=None):
+        self._chk(self._lib.tsp_iterate(self._h, int(n_iter), _stream_handle(stream)))
+
+    def read_image(self, which: int = 0, out=None, stream=None):
+        """rho (which=0) or rho' = s rho (which=1) as a CUDA tensor, or into
+        ``out`` (a CUDA tensor or a NumPy array)."""
+        if out is None:
+            out = torch.empty(self.ny, self.nz, dtype=torch.float32, device="cuda")
+        if isinstance(out, np.ndarray):
+            if out.dtype != np.float32 or not out.flags.c_contiguous or out.size != self.ny * self.nz:
+                raise ValueError("out must be a contiguous float32 array of ny*nz elements")
+            self._chk(self._lib.tsp_read_image(self._h, C.c_void_p(out.ctypes.data), int(which), 0,
+                                               _stream_handle(stream)))
+            return out
+        p, dev, keep = _arg(out)
+        if keep is not out:
+            raise ValueError("out must be a contiguous float32 CUDA tensor")
+        self._chk(self._lib.tsp_read_image(self._h, p, int(which), dev, _stream_handle(stream)))
+        return out
+
+    def loglik(self, stream=None) -> float:
+        v = C.c_double()
+        self._chk(self._lib.tsp_loglik(self._h, C.byref(v), _stream_handle(stream)))
+        return v.value
+
+    def loglik_grad(self, want_rho: bool = True, want_sigma: bool = True, stream=None):
+        """(L, g_rho as a CUDA tensor or None, g_sigma as a length-2 array or None)."""
+        v = C.c_double()
+        g = torch.empty(self.ny, self.nz, dtype=torch.float32, device="cuda") if want_rho else None
+        gs = (C.c_double * 2)() if want_sigma else None
+        self._chk(self._lib.tsp_loglik_grad(
+            self._h, C.byref(v), C.c_void_p(g.data_ptr()) if g is not None else None, 1,
+            gs, _stream_handle(stream)))
+        return v.value, g, (np.array([gs[0], gs[1]]) if gs is not None else None)
+
+    def set_sigma(self, sigma_z: float, sigma_dl: float, stream=None):
+        self._chk(self._lib.tsp_set_sigma(self._h, float(sigma_z), float(sigma_dl),
+                                          _stream_handle(stream)))
+        self.params.sigma_z = float(sigma_z)
+        self.params.sigma_dl = float(sigma_dl)
+
+    def stats(self, stream=None) -> dict:
+        s = L.Stats()
+        self._chk(self._lib.tsp_stats(self._h, C.byref(s), _stream_handle(stream)))
+        return {k: getattr(s, k) for k, _ in L.Stats._fields_}
+
+    def set_profiling(self, on: bool = True):
+        self._chk(self._lib.tsp_set_profiling(self._h, int(bool(on))))
+
+    def pass_times(self, max_count: int = 4096, stream=None):
+        """Device durations (ms) of the MLEM kernel launches of the last iterate."""
+        buf = (C.c_float * max_count)()
+        cnt = C.c_int()
+        self._chk(self._lib.tsp_pass_times(self._h, buf, max_count, C.byref(cnt),
+                                           _stream_handle(stream)))
+        return [buf[i] for i in range(cnt.value)]
+
+
+if torch is not None:
+
+    class LogLik(torch.autograd.Function):
+        """L(rho, sigma) = sum_j log D_j - sum_i s_i rho_i of a Recon's events,
+        with its gradient from the library's adjoint pass (denominators
+        recomputed, windows fixed at the evaluated sigma).
+
+        Usage: ``LogLik.apply(recon, rho, sigma)`` with rho a (ny, nz) CUDA
+        tensor and sigma a length-2 tensor (sigma_z, sigma_dl)."""
+
+        @staticmethod
+        def forward(ctx, recon: Recon, rho, sigma):
+            s = sigma.detach().double().cpu().numpy()
+            if (s[0], s[1]) != (recon.params.sigma_z, recon.params.sigma_dl):
+                recon.set_sigma(float(s[0]), float(s[1]))
+            recon.set_image(rho.detach().to(torch.float32).contiguous())
+            want_rho, want_sigma = ctx.needs_input_grad[1], ctx.needs_input_grad[2]
+            if want_rho or want_sigma:
+                val, g, gs = recon.loglik_grad(want_rho=want_rho, want_sigma=want_sigma)
+            else:
+                val, g, gs = recon.loglik(), None, None
+            ctx.g_rho = g
+            ctx.g_sigma = None if gs is None else torch.tensor(gs, dtype=sigma.dtype,
+                                                                device=sigma.device)
+            return torch.tensor(val, dtype=torch.float64, device=rho.device)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            go = float(grad_out)
+            g_rho = None if ctx.g_rho is None else ctx.g_rho * go
+            g_sig = None if ctx.g_sigma is None else ctx.g_sigma * go
+            return None, g_rho, g_sig
