@@ -36,6 +36,7 @@ struct tsp_ctx {
     long long n = 0, cap = 0;
     float *zu = nullptr, *zd = nullptr, *dl = nullptr;
     float4 *geo_u = nullptr, *geo = nullptr;
+    double4 *geo64_u = nullptr, *geo64 = nullptr;
     int2 *rows_u = nullptr, *rows = nullptr;
     int* key = nullptr;
     int4* items = nullptr;
@@ -150,6 +151,14 @@ int plan(tsp_ctx* c)
     g.kA = (float)std::sqrt(log2e / 2.0);
     g.half_log2e = (float)(log2e / 2.0);
     g.inv_sqrt_2iz = (float)(1.0 / std::sqrt(2.0 * iz));
+    g.y0d = -p.R + 0.5 * dy;
+    g.z0d = -0.5 * p.L + 0.5 * dz;
+    g.dyd = dy;
+    g.dzd = dz;
+    g.Rd = p.R;
+    g.izd = iz;
+    g.ild = il;
+    g.cut2d = cut * cut;
 
     // lane capacity: the longest chord of the ellipse is 2 cut sigma_z / sqrt(2)
     const double umax = cut * p.sigma_z / std::sqrt(2.0);
@@ -244,6 +253,7 @@ PassArgs pass_args(tsp_ctx* c)
     a.g = c->g;
     a.tl = c->tl;
     a.evs.geo = c->geo;
+    a.evs.geo64 = c->geo64;
     a.evs.rows = c->rows;
     a.items = c->items;
     a.n_items = c->n_items;
@@ -273,8 +283,8 @@ int prepare_events(tsp_ctx* c, cudaStream_t st)
     TSP_CUDA(c, cudaMemsetAsync(c->bin_count, 0, sizeof(int) * nbins, st));
     TSP_CUDA(c, cudaMemsetAsync(c->cursor, 0, sizeof(int) * nbins, st));
     TSP_CUDA(c, cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * 4, st));
-    TSP_CUDA(c, launch_setup(c->g, c->tl, n, c->zu, c->zd, c->dl, c->geo_u, c->rows_u, c->key,
-                             c->counters, c->bin_count, nbins, st));
+    TSP_CUDA(c, launch_setup(c->g, c->tl, n, c->zu, c->zd, c->dl, c->geo_u, c->geo64_u, c->rows_u,
+                             c->key, c->counters, c->bin_count, nbins, st));
     c->launches += n > 0 ? 1 : 0;
     std::vector<int> cnt(nbins);
     TSP_CUDA(c, cudaMemcpyAsync(c->counters_h, c->counters, sizeof(c->counters_h),
@@ -324,8 +334,8 @@ int prepare_events(tsp_ctx* c, cudaStream_t st)
                                     cudaMemcpyHostToDevice, st));
     TSP_CUDA(c, cudaMemcpyAsync(c->offsets, off.data(), sizeof(long long) * nbins,
                                 cudaMemcpyHostToDevice, st));
-    TSP_CUDA(c, launch_scatter(n, nbins, c->key, c->geo_u, c->rows_u, c->offsets, c->cursor, c->geo,
-                               c->rows, st));
+    TSP_CUDA(c, launch_scatter(n, nbins, c->key, c->geo_u, c->geo64_u, c->rows_u, c->offsets,
+                               c->cursor, c->geo, c->geo64, c->rows, st));
     c->launches += n > 0 ? 1 : 0;
     clear_graphs(c);
     c->uploaded = true;
@@ -340,6 +350,8 @@ int ensure_event_capacity(tsp_ctx* c, long long n)
     dfree(c->dl);
     dfree(c->geo_u);
     dfree(c->geo);
+    dfree(c->geo64_u);
+    dfree(c->geo64);
     dfree(c->rows_u);
     dfree(c->rows);
     dfree(c->key);
@@ -349,6 +361,8 @@ int ensure_event_capacity(tsp_ctx* c, long long n)
     TSP_CUDA(c, cudaMalloc(&c->dl, sizeof(float) * n));
     TSP_CUDA(c, cudaMalloc(&c->geo_u, sizeof(float4) * n));
     TSP_CUDA(c, cudaMalloc(&c->geo, sizeof(float4) * n));
+    TSP_CUDA(c, cudaMalloc(&c->geo64_u, sizeof(double4) * n));
+    TSP_CUDA(c, cudaMalloc(&c->geo64, sizeof(double4) * n));
     TSP_CUDA(c, cudaMalloc(&c->rows_u, sizeof(int2) * n));
     TSP_CUDA(c, cudaMalloc(&c->rows, sizeof(int2) * n));
     TSP_CUDA(c, cudaMalloc(&c->key, sizeof(int) * n));
@@ -370,9 +384,11 @@ int capture_iterations(tsp_ctx* c, int n_iter, tsp_ctx::Graph* out)
     cudaError_t e = cudaSuccess;
     for (int it = 0; it < n_iter && e == cudaSuccess; ++it) {
         e = launch_begin(c->accum, cs);
-        if (e == cudaSuccess && c->profiling) e = cudaEventRecord(ev[2 * it], cs);
+        if (e == cudaSuccess && c->profiling)
+            e = cudaEventRecordWithFlags(ev[2 * it], cs, cudaEventRecordExternal);
         if (e == cudaSuccess) e = launch_pass(c->lmax, kMlem, a, cs);
-        if (e == cudaSuccess && c->profiling) e = cudaEventRecord(ev[2 * it + 1], cs);
+        if (e == cudaSuccess && c->profiling)
+            e = cudaEventRecordWithFlags(ev[2 * it + 1], cs, cudaEventRecordExternal);
         if (e == cudaSuccess) e = launch_finalize(c->npix, c->rho, c->rhop, c->A, c->s, c->accum, cs);
     }
     cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
@@ -470,7 +486,8 @@ void tsp_destroy(tsp_ctx* c)
     dfree(c->rho); dfree(c->rhop); dfree(c->A); dfree(c->s); dfree(c->gbuf);
     dfree(c->accum); dfree(c->counters); dfree(c->flag);
     dfree(c->zu); dfree(c->zd); dfree(c->dl);
-    dfree(c->geo_u); dfree(c->geo); dfree(c->rows_u); dfree(c->rows); dfree(c->key);
+    dfree(c->geo_u); dfree(c->geo); dfree(c->geo64_u); dfree(c->geo64);
+    dfree(c->rows_u); dfree(c->rows); dfree(c->key);
     dfree(c->items); dfree(c->bin_count); dfree(c->offsets); dfree(c->cursor);
     delete c;
 }

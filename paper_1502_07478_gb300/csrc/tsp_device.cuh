@@ -40,6 +40,8 @@ struct Geo {
     float kA;               // sqrt(log2(e) / 2)
     float half_log2e;       // log2(e) / 2
     float inv_sqrt_2iz;     // 1 / sqrt(2 iz)
+    // double-precision copies for the exact window decision near its boundary
+    double y0d, z0d, dyd, dzd, Rd, izd, ild, cut2d;
 };
 
 // Image tiling used by the shared-memory accumulation.  Region of tile
@@ -67,8 +69,9 @@ struct Accum {
 
 // Prepared events in binned order.
 struct EventsView {
-    const float4* __restrict__ geo;  // (yt, zt, t, c2i) per event
-    const int2* __restrict__ rows;   // (first row, row count) of the non-empty chords
+    const float4* __restrict__ geo;    // (yt, zt, t, c2i) per event, rounded from geo64
+    const double4* __restrict__ geo64; // (yt, zt, t, c2i) in double precision
+    const int2* __restrict__ rows;     // (first row, row count) of the non-empty chords
 };
 
 // Key of an event in the binning: its tile index, the outlier bin (the last
@@ -101,16 +104,17 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// Eq. 2 (first forms) for one event; returns false for non-finite input.
+// Eq. 2 (first forms) for one event, in double precision; returns false for
+// non-finite input.  ev = (y~, z~, tan theta~, 1 + tan^2).
 __device__ __forceinline__ bool direct_reconstruction(const Geo& g, float zu, float zd, float dl,
-                                                      float4& ev)
+                                                      double4& ev)
 {
     if (!(isfinite(zu) && isfinite(zd) && isfinite(dl))) return false;
-    float t = (zu - zd) / (2.0f * g.R);
-    float c2i = fmaf(t, t, 1.0f);
-    float yt = -0.5f * dl / sqrtf(c2i);
-    float zt = fmaf(yt, t, 0.5f * (zu + zd));
-    ev = make_float4(yt, zt, t, c2i);
+    const double t = ((double)zu - (double)zd) / (2.0 * g.Rd);
+    const double c2i = 1.0 + t * t;
+    const double yt = -0.5 * (double)dl / sqrt(c2i);
+    const double zt = 0.5 * ((double)zu + (double)zd + 2.0 * yt * t);
+    ev = make_double4(yt, zt, t, c2i);
     return true;
 }
 
@@ -127,16 +131,46 @@ __device__ __forceinline__ int clamp_range(float flo, float fhi, int n, int& lo)
 
 // The chord of row iy inside the event's cut ellipse: pixel columns
 // [lo, lo + count) with bCb <= cut2 at their centres, clipped to the grid.
-// Also returns Dy, y and B0 = 4 il Dy^2 c2i, zc = zt + t Dy.
+// Also returns Dy, y and B0 = 4 il Dy^2 c2i, zc = zt + t Dy (single precision).
 struct Chord {
     int lo, count;
     float y, Dy, B0, zc;
 };
 
+// Margins of the single-precision window decision.  Its rounding error is
+// below 1e-4 pixel in the chord ends and below 1e-5 in rem = cut2 - B0 for
+// the workloads' coordinates; rows whose ends fall within these margins of a
+// pixel centre (or whose rem is near 0) are decided again in double precision,
+// so membership agrees with a double-precision evaluation of bCb <= cut^2.
+constexpr float kEndMargin = 1e-3f;   // pixels
+constexpr float kRemMargin = 5e-2f;
+
+__device__ __forceinline__ void chord_fp64(const Geo& g, const double4& e, int iy, int& lo,
+                                           int& count)
+{
+    const double y = g.y0d + (double)iy * g.dyd;
+    const double Dy = y - e.x;
+    const double rem = g.cut2d - 4.0 * g.ild * Dy * Dy * e.w;
+    lo = 0;
+    count = 0;
+    if (rem >= 0.0) {
+        const double umax = sqrt(rem / (2.0 * g.izd));
+        const double zc = e.y + e.z * Dy;
+        double flo = ceil((zc - umax - g.z0d) / g.dzd);
+        double fhi = floor((zc + umax - g.z0d) / g.dzd);
+        flo = fmin(fmax(flo, 0.0), (double)g.nz);
+        fhi = fmax(fmin(fhi, (double)(g.nz - 1)), -1.0);
+        lo = (int)flo;
+        const int hi = (int)fhi;
+        count = hi >= lo ? hi - lo + 1 : 0;
+    }
+}
+
 // Explicitly rounded operations (never contracted into FMAs), so that the
 // event preparation and the MLEM passes derive bit-identical chords whatever
 // the surrounding code lets the compiler fuse.
-__device__ __forceinline__ Chord row_chord(const Geo& g, const float4& ev, int iy)
+__device__ __forceinline__ Chord row_chord(const Geo& g, const float4& ev,
+                                           const double4* __restrict__ ev64, int iy)
 {
     Chord c;
     c.y = __fmaf_rn((float)iy, g.dy, g.y0);
@@ -146,12 +180,16 @@ __device__ __forceinline__ Chord row_chord(const Geo& g, const float4& ev, int i
     c.lo = 0;
     c.count = 0;
     const float rem = __fsub_rn(g.cut2, c.B0);
+    bool unsure = fabsf(rem) < kRemMargin;
     if (rem >= 0.0f) {
         const float umax = __fmul_rn(__fsqrt_rn(rem), g.inv_sqrt_2iz);
-        const float flo = ceilf(__fmul_rn(__fsub_rn(__fsub_rn(c.zc, umax), g.z0), g.inv_dz));
-        const float fhi = floorf(__fmul_rn(__fsub_rn(__fadd_rn(c.zc, umax), g.z0), g.inv_dz));
-        c.count = clamp_range(flo, fhi, g.nz, c.lo);
+        const float xlo = __fmul_rn(__fsub_rn(__fsub_rn(c.zc, umax), g.z0), g.inv_dz);
+        const float xhi = __fmul_rn(__fsub_rn(__fadd_rn(c.zc, umax), g.z0), g.inv_dz);
+        unsure = unsure || fabsf(xlo - rintf(xlo)) < kEndMargin ||
+                 fabsf(xhi - rintf(xhi)) < kEndMargin;
+        c.count = clamp_range(ceilf(xlo), floorf(xhi), g.nz, c.lo);
     }
+    if (unsure) chord_fp64(g, *ev64, iy, c.lo, c.count);
     return c;
 }
 

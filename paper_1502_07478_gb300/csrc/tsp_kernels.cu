@@ -59,7 +59,8 @@ __global__ void k_sensitivity(double R, double L, int ny, int nz, double dy, dou
 // bin_count has nbins entries; the last bin collects the outliers.
 __global__ void k_setup(Geo g, Tiling tl, long long n, const float* __restrict__ zu,
                         const float* __restrict__ zd, const float* __restrict__ dl,
-                        float4* __restrict__ geo, int2* __restrict__ rows, int* __restrict__ key,
+                        float4* __restrict__ geo, double4* __restrict__ geo64,
+                        int2* __restrict__ rows, int* __restrict__ key,
                         unsigned long long* counters, int* bin_count, int nbins)
 {
     extern __shared__ int s_hist[];
@@ -71,18 +72,20 @@ __global__ void k_setup(Geo g, Tiling tl, long long n, const float* __restrict__
     unsigned long long bad = 0, empty = 0, outl = 0, pix = 0;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
          j += (long long)gridDim.x * blockDim.x) {
+        double4 e64 = make_double4(0.0, 0.0, 0.0, 1.0);
         float4 ev = make_float4(0.f, 0.f, 0.f, 1.f);
         int k = kKeyEmpty;
         int2 rw = make_int2(0, 0);
-        if (!direct_reconstruction(g, zu[j], zd[j], dl[j], ev)) {
+        if (!direct_reconstruction(g, zu[j], zd[j], dl[j], e64)) {
             ++bad;
         } else {
+            ev = make_float4((float)e64.x, (float)e64.y, (float)e64.z, (float)e64.w);
             int iy_lo, nrows, iz_lo, ncols;
             event_bbox(g, ev, iy_lo, nrows, iz_lo, ncols);
             int first = -1, last = -1, zmin = INT_MAX, zmax = -1;
             unsigned long long cnt = 0;
             for (int r = 0; r < nrows; ++r) {
-                const Chord c = row_chord(g, ev, iy_lo + r);
+                const Chord c = row_chord(g, ev, &e64, iy_lo + r);
                 if (c.count > 0) {
                     if (first < 0) first = iy_lo + r;
                     last = iy_lo + r;
@@ -109,6 +112,7 @@ __global__ void k_setup(Geo g, Tiling tl, long long n, const float* __restrict__
             }
         }
         geo[j] = ev;
+        geo64[j] = e64;
         rows[j] = rw;
         key[j] = k;
         if (k >= 0) {
@@ -141,9 +145,10 @@ __global__ void k_setup(Geo g, Tiling tl, long long n, const float* __restrict__
 // block the rank of an event in its bin comes from a shared-memory counter and
 // one global reservation is made per (block, bin).
 __global__ void k_scatter(long long n, int nbins, const int* __restrict__ key,
-                          const float4* __restrict__ geo_in, const int2* __restrict__ rows_in,
-                          const long long* __restrict__ offsets, int* cursor,
-                          float4* __restrict__ geo_out, int2* __restrict__ rows_out)
+                          const float4* __restrict__ geo_in, const double4* __restrict__ g64_in,
+                          const int2* __restrict__ rows_in, const long long* __restrict__ offsets,
+                          int* cursor, float4* __restrict__ geo_out, double4* __restrict__ g64_out,
+                          int2* __restrict__ rows_out)
 {
     extern __shared__ int s_cnt[];   // [nbins] local counts, then [nbins] reserved bases
     int* s_base = s_cnt + nbins;
@@ -162,14 +167,18 @@ __global__ void k_scatter(long long n, int nbins, const int* __restrict__ key,
     if (k >= 0) {
         const long long pos = offsets[k] + s_base[k] + rank;
         geo_out[pos] = geo_in[j];
+        g64_out[pos] = g64_in[j];
         rows_out[pos] = rows_in[j];
     }
 }
 
 __global__ void k_scatter_global(long long n, const int* __restrict__ key,
-                                 const float4* __restrict__ geo_in, const int2* __restrict__ rows_in,
+                                 const float4* __restrict__ geo_in,
+                                 const double4* __restrict__ g64_in,
+                                 const int2* __restrict__ rows_in,
                                  const long long* __restrict__ offsets, int* cursor,
-                                 float4* __restrict__ geo_out, int2* __restrict__ rows_out)
+                                 float4* __restrict__ geo_out, double4* __restrict__ g64_out,
+                                 int2* __restrict__ rows_out)
 {
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
          j += (long long)gridDim.x * blockDim.x) {
@@ -177,6 +186,7 @@ __global__ void k_scatter_global(long long n, const int* __restrict__ key,
         if (k < 0) continue;
         const long long pos = offsets[k] + atomicAdd(&cursor[k], 1);
         geo_out[pos] = geo_in[j];
+        g64_out[pos] = g64_in[j];
         rows_out[pos] = rows_in[j];
     }
 }
@@ -275,28 +285,31 @@ cudaError_t launch_sensitivity(double R, double L, int ny, int nz, double dy, do
 }
 
 cudaError_t launch_setup(const Geo& g, const Tiling& tl, long long n, const float* zu,
-                         const float* zd, const float* dl, float4* geo, int2* rows, int* key,
-                         unsigned long long* counters, int* bin_count, int nbins, cudaStream_t st)
+                         const float* zd, const float* dl, float4* geo, double4* geo64, int2* rows,
+                         int* key, unsigned long long* counters, int* bin_count, int nbins,
+                         cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const size_t smem = nbins <= 8192 ? (size_t)nbins * sizeof(int) : 0;
     k_setup<<<blocks_for(n, kAuxThreads * 8, 4096), kAuxThreads, smem, st>>>(
-        g, tl, n, zu, zd, dl, geo, rows, key, counters, bin_count, nbins);
+        g, tl, n, zu, zd, dl, geo, geo64, rows, key, counters, bin_count, nbins);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(long long n, int nbins, const int* key, const float4* geo_in,
-                           const int2* rows_in, const long long* offsets, int* cursor,
-                           float4* geo_out, int2* rows_out, cudaStream_t st)
+                           const double4* g64_in, const int2* rows_in, const long long* offsets,
+                           int* cursor, float4* geo_out, double4* g64_out, int2* rows_out,
+                           cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     if (nbins <= 4096) {
         k_scatter<<<blocks_for(n, kAuxThreads * 4, INT_MAX), kAuxThreads * 4,
-                    2 * (size_t)nbins * sizeof(int), st>>>(n, nbins, key, geo_in, rows_in, offsets,
-                                                           cursor, geo_out, rows_out);
+                    2 * (size_t)nbins * sizeof(int), st>>>(n, nbins, key, geo_in, g64_in, rows_in,
+                                                           offsets, cursor, geo_out, g64_out,
+                                                           rows_out);
     } else {
         k_scatter_global<<<blocks_for(n, kAuxThreads, 4096), kAuxThreads, 0, st>>>(
-            n, key, geo_in, rows_in, offsets, cursor, geo_out, rows_out);
+            n, key, geo_in, g64_in, rows_in, offsets, cursor, geo_out, g64_out, rows_out);
     }
     return cudaGetLastError();
 }

@@ -63,12 +63,13 @@ __device__ __forceinline__ void row_idle(RowK& r, RowG& rg)
 // preparation guarantees that every chord lies inside that extent; the clamp
 // below keeps every access in bounds regardless (clipped pixels are counted).
 template <int LMAX, bool GRAD>
-__device__ __forceinline__ void make_row(const Geo& g, const float4& ev, int iy, int seg,
-                                         int oy, int oz, int stride, int rh, int rw, RowK& r,
-                                         RowG& rg, unsigned& qclip, unsigned& lclip)
+__device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const double4* ev64,
+                                         int iy, int seg, int oy, int oz, int stride, int rh,
+                                         int rw, RowK& r, RowG& rg, unsigned& qclip,
+                                         unsigned& lclip)
 {
     row_idle<GRAD>(r, rg);
-    Chord c = row_chord(g, ev, iy);
+    Chord c = row_chord(g, ev, ev64, iy);
     int lo = c.lo + seg * LMAX;
     int hi = c.lo + c.count - 1;                     // last chord pixel
     if (iy < oy || iy >= oy + rh) {
@@ -228,7 +229,8 @@ __device__ __forceinline__ void process_event(const Geo& g, const EventsView& ev
     RowK r;
     RowG rg;
     if (rowi < rws.y)
-        make_row<LMAX, GRAD>(g, ev, rws.x + rowi, seg, oy, oz, stride, rh, rw, r, rg, qclip, lclip);
+        make_row<LMAX, GRAD>(g, ev, evs.geo64 + e, rws.x + rowi, seg, oy, oz, stride, rh, rw, r,
+                             rg, qclip, lclip);
     else
         row_idle<GRAD>(r, rg);
     const int maxlen = __reduce_max_sync(0xffffffffu, (unsigned)r.len);
