@@ -97,11 +97,14 @@ def test_adam_recovers_sigma():
     rho = torch.tensor(truth, dtype=torch.float32, device="cuda")
     logsig = torch.tensor(np.log([14.0, 55.0]), dtype=torch.float64, requires_grad=True)
     opt = torch.optim.Adam([logsig], lr=1e-2)
+    # decay lr from 1e-2 to 1e-4 over the 500 steps so the iterate settles
+    sched = torch.optim.lr_scheduler.ExponentialLR(opt, gamma=0.01 ** (1 / 500))
     for _ in range(500):
         opt.zero_grad()
         loss = -LogLik.apply(r, rho, torch.exp(logsig)) / w.n_events
         loss.backward()
         opt.step()
+        sched.step()
     sig = torch.exp(logsig).detach().numpy()
     print("fitted sigma", sig)
     assert abs(sig[0] / w.sigma_z - 1) < 0.03, sig
