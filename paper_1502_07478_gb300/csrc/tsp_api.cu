@@ -163,47 +163,63 @@ int plan(tsp_ctx* c)
     // lane capacity: the longest chord of the ellipse is 2 cut sigma_z / sqrt(2)
     const double umax = cut * p.sigma_z / std::sqrt(2.0);
     const int need = (int)std::floor(2.0 * umax / dz) + 2;
+    // one lane per row (whole chord), or two lanes per row (one per half)
     int best_l = 0, best_s = 0;
-    for (int nseg = 1; nseg <= 4 && !best_l; ++nseg)
-        for (int k = 0; k < kLmaxCount; ++k)
-            if (kLmaxList[k] * nseg >= need) {
-                best_l = kLmaxList[k];
-                best_s = nseg;
-                break;
-            }
+    for (int k = 0; k < kLmaxCount && !best_l; ++k)
+        if (kLmaxList[k] >= need) {
+            best_l = kLmaxList[k];
+            best_s = 1;
+        }
+    for (int k = 0; k < kLmaxCount && !best_l; ++k)
+        if (kLmaxList[k] >= need / 2 + 2) {
+            best_l = kLmaxList[k];
+            best_s = 2;
+        }
     if (!best_l) return fail(c, TSP_EINVAL, "window chords too long for the compiled lane capacities");
     c->lmax = best_l;
     c->nseg = best_s;
     // rows of a window: |Dy| <= cut sigma_dl cos / 2
     const double hy = cut * p.sigma_dl / 2.0 * 1.00001;
     const int maxrows = (int)std::floor(2.0 * hy / dy) + 2;
-    const int lanes = maxrows * c->nseg;
-    c->G = (lanes + 31) / 32;
+    c->G = c->nseg * ((maxrows + 31) / 32);
     if (c->G > kWarps) return fail(c, TSP_EINVAL, "window has more rows than one block can hold");
 
-    // tiling: halo holds every window whose centre lies in the tile, for
-    // |tan theta~| <= 1; wider windows go to the outlier path.
+    // tiling (see Tiling): angle bins of width 1/16 in tan(theta~) cover the
+    // accepted range |t| <= L/2R widened by 6 sigma of its measurement noise
+    // (sqrt(2) sigma_z / 2R); events outside go to the outlier path.
     Tiling& tl = c->tl;
+    const double dtb = 1.0 / 16.0;
+    const double t_max = p.L / (2.0 * p.R) + 6.0 * std::sqrt(2.0) * p.sigma_z / (2.0 * p.R);
+    tl.nb = (int)std::ceil(2.0 * t_max / dtb);
+    tl.dtb = (float)dtb;
+    tl.inv_dtb = (float)(1.0 / dtb);
+    tl.t0 = (float)(-0.5 * tl.nb * dtb);
+    tl.rho_yz = (float)(dy / dz);
+    tl.Y0 = p.ny / 2;
+    const double smax = (0.5 * tl.nb * dtb) * (dy / dz);
+    tl.zs_off = (int)std::ceil(smax * (p.ny / 2 + 1)) + 1;
     tl.HY = (int)std::ceil(hy / dy) + 1;
-    const double hz_cap = std::sqrt(cut * cut * p.sigma_z * p.sigma_z / 2.0 +
-                                    cut * cut * p.sigma_dl * p.sigma_dl * 0.5 / 4.0) * 1.00001;
-    tl.HZ = (int)std::ceil(hz_cap / dz) + 1;
+    // chord half-width, plus the drift of chord centres from the event's
+    // sheared centre column: rounding (1.5), sub-pixel centre (|t| rho / 2) and
+    // the in-bin angle spread over the rows ((dtb/2) rho HY)
+    const double w = umax / dz;
+    tl.HZ = (int)std::ceil(w + 1.5 + 0.5 * t_max * (dy / dz) + 0.5 * dtb * (dy / dz) * tl.HY) + 1;
     int RS = 33;
     while (RS - 2 * tl.HZ < std::min(16, p.nz)) RS += 32;
     tl.RS = RS;
     tl.RW = RS;
     tl.TZ = RS - 2 * tl.HZ;
     const size_t budget = 200 * 1024;
-    const size_t fixed = (size_t)(kPadFloats + kWarps * 6) * sizeof(float);
-    int rh_max = (int)((budget - fixed) / (2 * sizeof(float) * (size_t)RS));
-    tl.TY = std::min(64, rh_max - 2 * tl.HY);
-    if (tl.TY < 4) return fail(c, TSP_EINVAL, "window halo too large for shared memory");
-    tl.TY = std::min(tl.TY, std::max(p.ny, 4));
+    int TY = 128;
+    while (TY > 4 && tiles_smem_floats(TY + 2 * tl.HY, RS) * sizeof(float) > budget) TY -= 4;
+    if (tiles_smem_floats(TY + 2 * tl.HY, RS) * sizeof(float) > budget)
+        return fail(c, TSP_EINVAL, "window halo too large for shared memory");
+    tl.TY = std::min(TY, std::max(p.ny, 4));
     tl.RH = tl.TY + 2 * tl.HY;
     tl.tiles_y = (p.ny + tl.TY - 1) / tl.TY;
-    tl.tiles_z = (p.nz + tl.TZ - 1) / tl.TZ;
-    c->smem = (size_t)(2 * tl.RH * tl.RS) * sizeof(float) + fixed;
-    c->nbins = tl.tiles_y * tl.tiles_z + 1;
+    tl.tiles_z = (p.nz + 2 * tl.zs_off + tl.TZ - 1) / tl.TZ;
+    c->smem = tiles_smem_floats(tl.RH, tl.RS) * sizeof(float);
+    c->nbins = tl.nb * tl.tiles_y * tl.tiles_z + 1;
     for (int mode = 0; mode < 3; ++mode) {
         cudaError_t e = prepare_pass(c->lmax, mode, c->smem);
         if (e != cudaSuccess)

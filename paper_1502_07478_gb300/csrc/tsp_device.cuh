@@ -44,14 +44,47 @@ struct Geo {
     double y0d, z0d, dyd, dzd, Rd, izd, ild, cut2d;
 };
 
-// Image tiling used by the shared-memory accumulation.  Region of tile
-// (ty, tz): rows [ty*TY - HY, +RH), columns [tz*TZ - HZ, +RW), stored with row
-// stride RS floats.
+// Image tiling used by the shared-memory accumulation.
+//
+// Events are binned by the angle bin b of tan(theta~) (width dtb, starting at
+// t0) and by a tile of a sheared image frame: column iz of row iy has sheared
+// coordinate z' = iz - shift_b(iy) + zs_off with
+//   shift_b(iy) = rint(s_b * (iy - Y0)),  s_b = (t0 + (b + 1/2) dtb) dy/dz,
+// the shift that lines up the chord centres of events with tan(theta~) near
+// the bin centre.  Tile (b, ty, tz) holds the events whose window-centre pixel
+// has row in [ty TY, +TY) and sheared column in [tz TZ, +TZ).  Its staged
+// region has RH = TY + 2 HY rows starting at row ty TY - HY; region row iy
+// starts at image column  tz TZ - HZ - zs_off + shift_b(iy)  and is RW columns
+// wide, stored with row stride RS floats.  Bin index = (b*tiles_y + ty)*tiles_z
+// + tz; one more bin collects the outliers.
 struct Tiling {
     int TY, TZ, HY, HZ;
     int RH, RW, RS;
-    int tiles_y, tiles_z;
+    int tiles_y, tiles_z, nb;
+    float t0, dtb, inv_dtb;
+    float rho_yz;              // dy / dz
+    int Y0, zs_off;
 };
+
+__device__ __forceinline__ float bin_shear(const Tiling& tl, int b)
+{
+    return __fmul_rn(__fmaf_rn((float)b + 0.5f, tl.dtb, tl.t0), tl.rho_yz);
+}
+
+__device__ __forceinline__ int row_shift(const Tiling& tl, float shear, int iy)
+{
+    return (int)rintf(__fmul_rn(shear, (float)(iy - tl.Y0)));
+}
+
+// Shared-memory layout of the tile kernel, in floats: kPadFloats slack, the
+// rho' region (RH*RS), 2*kPadFloats slack, the accumulator region (RH*RS),
+// kPadFloats slack, then the groups' reduction slots (kWarps/G groups x 2
+// parities x 3G floats <= 6*kWarps).
+__host__ __device__ constexpr size_t tiles_smem_floats(int RH, int RS)
+{
+    return (size_t)kPadFloats + (size_t)RH * RS + 2 * kPadFloats + (size_t)RH * RS + kPadFloats +
+           6 * kWarps;
+}
 
 // Device-side accumulators of one pass.
 struct Accum {
@@ -137,13 +170,16 @@ struct Chord {
     float y, Dy, B0, zc;
 };
 
-// Margins of the single-precision window decision.  Its rounding error is
-// below 1e-4 pixel in the chord ends and below 1e-5 in rem = cut2 - B0 for
-// the workloads' coordinates; rows whose ends fall within these margins of a
-// pixel centre (or whose rem is near 0) are decided again in double precision,
-// so membership agrees with a double-precision evaluation of bCb <= cut^2.
-constexpr float kEndMargin = 1e-3f;   // pixels
-constexpr float kRemMargin = 5e-2f;
+// The single-precision window decision is repeated in double precision when a
+// chord end lies within a bound on its rounding error of a pixel centre, or
+// when rem = cut2 - B0 is within its own error bound of 0, so that membership
+// agrees with a double-precision evaluation of bCb <= cut^2.  The bounds are a
+// few times the worst-case error of the single-precision expressions:
+//   end:  kEndRel * (|x| + (|zc| + umax + |z0|)/dz)            (coordinates)
+//       + kEndRel * cut2 / sqrt(rem) / sqrt(2 iz) / dz           (from umax)
+//   rem:  kRemRel * cut2
+constexpr float kEndRel = 1e-6f;
+constexpr float kRemRel = 1e-5f;
 
 __device__ __forceinline__ void chord_fp64(const Geo& g, const double4& e, int iy, int& lo,
                                            int& count)
@@ -180,13 +216,16 @@ __device__ __forceinline__ Chord row_chord(const Geo& g, const float4& ev,
     c.lo = 0;
     c.count = 0;
     const float rem = __fsub_rn(g.cut2, c.B0);
-    bool unsure = fabsf(rem) < kRemMargin;
+    bool unsure = fabsf(rem) < kRemRel * g.cut2;
     if (rem >= 0.0f) {
-        const float umax = __fmul_rn(__fsqrt_rn(rem), g.inv_sqrt_2iz);
+        const float sr = __fsqrt_rn(rem);
+        const float umax = __fmul_rn(sr, g.inv_sqrt_2iz);
         const float xlo = __fmul_rn(__fsub_rn(__fsub_rn(c.zc, umax), g.z0), g.inv_dz);
         const float xhi = __fmul_rn(__fsub_rn(__fadd_rn(c.zc, umax), g.z0), g.inv_dz);
-        unsure = unsure || fabsf(xlo - rintf(xlo)) < kEndMargin ||
-                 fabsf(xhi - rintf(xhi)) < kEndMargin;
+        const float coord = (fabsf(c.zc) + umax + fabsf(g.z0)) * g.inv_dz;
+        const float m = kEndRel * (fabsf(xhi) + coord) +
+                        kEndRel * g.cut2 * g.inv_sqrt_2iz * g.inv_dz / fmaxf(sr, 1e-20f);
+        unsure = unsure || fabsf(xlo - rintf(xlo)) < m || fabsf(xhi - rintf(xhi)) < m;
         c.count = clamp_range(ceilf(xlo), floorf(xhi), g.nz, c.lo);
     }
     if (unsure) chord_fp64(g, *ev64, iy, c.lo, c.count);

@@ -82,16 +82,32 @@ __global__ void k_setup(Geo g, Tiling tl, long long n, const float* __restrict__
             ev = make_float4((float)e64.x, (float)e64.y, (float)e64.z, (float)e64.w);
             int iy_lo, nrows, iz_lo, ncols;
             event_bbox(g, ev, iy_lo, nrows, iz_lo, ncols);
-            int first = -1, last = -1, zmin = INT_MAX, zmax = -1;
+            // angle bin and sheared tile of the pixel holding the window centre
+            const float fb = floorf((ev.z - tl.t0) * tl.inv_dtb);
+            const bool bin_ok = fb >= 0.0f && fb < (float)tl.nb;
+            const int b = bin_ok ? (int)fb : 0;
+            const float shear = bin_shear(tl, b);
+            const int iyc = (int)fminf(fmaxf(floorf((ev.x - g.y0) * g.inv_dy + 0.5f), 0.f),
+                                       (float)(g.ny - 1));
+            const int izc = (int)fminf(fmaxf(floorf((ev.y - g.z0) * g.inv_dz + 0.5f), 0.f),
+                                       (float)(g.nz - 1));
+            const int zp = min(max(izc - row_shift(tl, shear, iyc) + tl.zs_off, 0),
+                               tl.tiles_z * tl.TZ - 1);
+            const int ty = iyc / tl.TY, tz = zp / tl.TZ;
+            const int oy = ty * tl.TY - tl.HY, zbase = tz * tl.TZ - tl.HZ - tl.zs_off;
+            bool fits = bin_ok;
+            int first = -1, last = -1;
             unsigned long long cnt = 0;
             for (int r = 0; r < nrows; ++r) {
-                const Chord c = row_chord(g, ev, &e64, iy_lo + r);
+                const int iy = iy_lo + r;
+                const Chord c = row_chord(g, ev, &e64, iy);
                 if (c.count > 0) {
-                    if (first < 0) first = iy_lo + r;
-                    last = iy_lo + r;
+                    if (first < 0) first = iy;
+                    last = iy;
                     cnt += (unsigned long long)c.count;
-                    zmin = min(zmin, c.lo);
-                    zmax = max(zmax, c.lo + c.count - 1);
+                    const int z0row = zbase + row_shift(tl, shear, iy);
+                    fits = fits && iy >= oy && iy < oy + tl.RH && c.lo >= z0row &&
+                           c.lo + c.count <= z0row + tl.RW;
                 }
             }
             if (cnt == 0) {
@@ -99,15 +115,7 @@ __global__ void k_setup(Geo g, Tiling tl, long long n, const float* __restrict__
             } else {
                 pix += cnt;
                 rw = make_int2(first, last - first + 1);
-                // tile of the pixel holding the window centre (clamped to the grid)
-                const float fy = fminf(fmaxf(floorf((ev.x - g.y0) * g.inv_dy + 0.5f), 0.f),
-                                       (float)(g.ny - 1));
-                const float fz = fminf(fmaxf(floorf((ev.y - g.z0) * g.inv_dz + 0.5f), 0.f),
-                                       (float)(g.nz - 1));
-                const int ty = (int)fy / tl.TY, tz = (int)fz / tl.TZ;
-                const int oy = ty * tl.TY - tl.HY, oz = tz * tl.TZ - tl.HZ;
-                const bool fits = first >= oy && last < oy + tl.RH && zmin >= oz && zmax < oz + tl.RW;
-                k = fits ? ty * tl.tiles_z + tz : nbins - 1;
+                k = fits ? (b * tl.tiles_y + ty) * tl.tiles_z + tz : nbins - 1;
                 if (!fits) ++outl;
             }
         }

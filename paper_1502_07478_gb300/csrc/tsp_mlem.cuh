@@ -1,43 +1,75 @@
 // The list-mode MLEM hot path (Eq. iter with Eq. kernel over 3-sigma windows).
 //
-// One persistent block per SM pulls work items (an image tile and a run of the
-// events whose window centre lies in it) from an atomic queue.  For each item it
-// stages rho' = s*rho of the tile plus a halo that holds every window of those
-// events in shared memory and zeroes an accumulator of the same shape.  Warps
-// are grouped (G warps per group); a group takes one event at a time and each of
-// its lanes takes one image row of the event's window (or one segment of it):
-//   pass 1: walk the lane's chord of the ellipse, evaluate P (Eq. kernel) in the
-//           log2 domain (one rsqrt and one ex2 per pixel), keep P in registers
-//           and accumulate D_j = sum P rho' (the denominator of Eq. iter);
-//           warp shuffles and one named barrier reduce D_j over the group;
-//   pass 2: add P / D_j into the shared accumulator (shared-memory atomics; two
+// One persistent block per SM pulls work items (an angle bin, an image tile of
+// that bin's sheared frame, and a run of the events whose window-centre pixel
+// lies in the tile) from an atomic queue.  For each item it stages rho' = s*rho
+// of the tile's region in shared memory, row by row in the bin's sheared frame
+// (so that the chords of all its events are centred on nearly the same stored
+// column), and zeroes an accumulator of the same shape.  Warps are grouped (G
+// warps per group); a group takes one event at a time and each lane takes one
+// image row of the event's window (or one side of it):
+//   pass 1: walk the lane's chord of the ellipse outward from its centre,
+//           evaluate P (Eq. kernel) in the log2 domain (one rsqrt and one ex2
+//           per pixel), keep P in registers and accumulate D_j = sum P rho'
+//           (the denominator of Eq. iter); warp shuffles and a named barrier
+//           reduce D_j over the group;
+//   pass 2: add P / D_j into the shared accumulator (shared-memory atomics: two
 //           groups may touch the same pixel).
+// Neighbouring lanes hold neighbouring rows; with the sheared frame and a row
+// stride of 1 mod 32 words their accesses at each step fall in distinct banks.
 // At the end of the item the accumulator is flushed to the global
 // back-projection A with one atomic add per touched pixel; the finalize kernel
-// then forms rho <- rho * A.  This replaces the paper's warp-per-event kernel
-// with texture reads (Sec. 4.2) by row-per-lane evaluation, a register cache of
-// P between the passes (the paper caches in shared memory and registers too),
-// and shared-memory accumulation of the scatter.
+// then forms rho <- rho * A.
+//
+// Relative to the paper's GPU design (one warp per event over its bounding
+// box, rho read through the texture cache, Sec. 4.2): lanes own chords of the
+// ellipse instead of bounding-box pixels (no ellipse-test waste), P is cached
+// in registers between the two passes as in the paper, and the scatter goes to
+// shared memory first.
 #pragma once
 
 #include "tsp_device.cuh"
 
 namespace tsp {
 
-// Per-lane row constants.  For m = 0 .. len-1 the lane's pixel m has
-//   u = u0 + m dz,  Q = aCa + 2 oCb = Q0 + m dQ,
-//   A = sqrt(log2e/2) aCb = A0 + m dA,  s = sqrt(log2e iz) u = su0 + m dsu,
+// Pixel order of a lane's chord, relative to its centre column c:
+//   kAlt: 0, +1, -1, +2, -2, ...  (whole chord, one lane per row)
+//   kPos: 0, +1, +2, ...          (right half, when a row is split over two lanes)
+//   kNeg: -1, -2, ...             (left half)
+enum Trav : int { kAlt = 0, kPos = 1, kNeg = 2 };
+
+template <int TRAV>
+__host__ __device__ constexpr int trav_delta(int m)
+{
+    return TRAV == kAlt ? ((m & 1) ? (m + 1) / 2 : -(m / 2)) : (TRAV == kPos ? m : -(m + 1));
+}
+
+// Storage frame of a lane's buffer: row iy of the image is stored at
+// (iy - oy) * stride; its image column iz at column iz - (zbase + shift(iy)),
+// shift(iy) = rint(shear * (iy - Y0)).  Extent rh x rw.
+struct Frame {
+    int oy, zbase, Y0, stride, rh, rw;
+    float shear;
+};
+
+// Per-lane row constants, relative to the lane's chord centre c.  For step m
+// with d = trav_delta(m):
+//   u = u0 + d dz,  Q = aCa + 2 oCb = Q0 + d dQ,
+//   A = sqrt(log2e/2) aCb = A0 + d dA,  s = sqrt(log2e iz) u = su0 + d dsu,
 // and Eq. kernel becomes
 //   P = Q^(-1/2) 2^(C0 - s^2 + A^2/Q),  C0 = log2 K - (log2e/2) 4 il Dy^2 c2i,
-// K = det^(1/2)(C^-1) / (2 pi^2) (reading R4).
+// K = det^(1/2)(C^-1) / (2 pi^2) (reading R4).  sbase / gbase is the byte
+// address of pixel c in the shared window or in the global image.
 struct RowK {
-    int len, sbase;
+    int len;
+    unsigned sbase;
+    unsigned long long gbase;
     float Q0, dQ, A0, dA, su0, dsu, C0;
 };
 
 // Extra row constants of the sigma-gradient (adjoint) pass:
-//   u = u0 + m du, aCb = b0 + m db (unscaled), Qz/2 = qz0 + m dqz,
-//   Cz = cz0 + m dcz, and the row constants kz = 1/iz, kl = 1/(2 il) - Bl/2,
+//   u = u0 + d du, aCb = b0 + d db (unscaled), Qz/2 = qz0 + d dqz,
+//   Cz = cz0 + d dcz, and the row constants kz = 1/iz, kl = 1/(2 il) - Bl/2,
 //   Cl, Ql/2 (see the derivative formulas in the gradient pass).
 struct RowG {
     float u0, du, b0, db, qz0, dqz, cz0, dcz, kz, kl, cl, qlh;
@@ -50,6 +82,7 @@ __device__ __forceinline__ void row_idle(RowK& r, RowG& rg)
 {
     r.len = 0;
     r.sbase = 0;
+    r.gbase = 0;
     r.Q0 = 1.0f; r.dQ = 0.0f; r.A0 = 0.0f; r.dA = 0.0f; r.su0 = 0.0f; r.dsu = 0.0f;
     r.C0 = -126.0f;
     if (GRAD) {
@@ -58,66 +91,80 @@ __device__ __forceinline__ void row_idle(RowK& r, RowG& rg)
     }
 }
 
-// Row constants of lane row iy (segment seg) for a buffer whose element 0 is
-// pixel (oy, oz), with row stride `stride` and extent rh x rw.  The event
-// preparation guarantees that every chord lies inside that extent; the clamp
-// below keeps every access in bounds regardless (clipped pixels are counted).
-template <int LMAX, bool GRAD>
+// Row constants of lane row iy for the traversal TRAV.  The event preparation
+// guarantees that every chord lies inside the frame; the clamp keeps every
+// access in bounds regardless (clipped pixels are counted).
+template <int TRAV, bool GRAD, bool SMEM>
 __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const double4* ev64,
-                                         int iy, int seg, int oy, int oz, int stride, int rh,
-                                         int rw, RowK& r, RowG& rg, unsigned& qclip,
-                                         unsigned& lclip)
+                                         int iy, const Frame& f, const float* base, RowK& r,
+                                         RowG& rg, unsigned& qclip, unsigned& lclip)
 {
     row_idle<GRAD>(r, rg);
-    Chord c = row_chord(g, ev, ev64, iy);
-    int lo = c.lo + seg * LMAX;
-    int hi = c.lo + c.count - 1;                     // last chord pixel
-    if (iy < oy || iy >= oy + rh) {
-        lclip += (unsigned)max(c.count, 0);
+    const Chord c = row_chord(g, ev, ev64, iy);
+    if (c.count <= 0) return;
+    int lo = c.lo, hi = c.lo + c.count - 1;
+    if (iy < f.oy || iy >= f.oy + f.rh) {
+        lclip += (unsigned)c.count;
         return;
     }
-    if (lo < oz || hi >= oz + rw) {
-        const int lo2 = max(lo, oz), hi2 = min(hi, oz + rw - 1);
-        lclip += (unsigned)(max(hi - lo + 1, 0) - max(hi2 - lo2 + 1, 0));
+    const int z0row = f.zbase + (int)rintf(__fmul_rn(f.shear, (float)(iy - f.Y0)));
+    if (lo < z0row || hi >= z0row + f.rw) {
+        const int lo2 = max(lo, z0row), hi2 = min(hi, z0row + f.rw - 1);
+        lclip += (unsigned)(c.count - max(hi2 - lo2 + 1, 0));
         lo = lo2;
         hi = hi2;
+        if (hi < lo) return;
     }
-    int len = min(hi - lo + 1, LMAX);
-    if (len <= 0) return;
     const float t = ev.z, c2i = ev.w, y = c.y, Dy = c.Dy;
-    float u0 = fmaf((float)lo, g.dz, g.z0) - c.zc;
-    float y2 = y * y;
-    float aCa = 2.0f * g.iz * (g.R * g.R + y2) * c2i * c2i + 4.0f * g.il * y2 * t * t * c2i;
-    float two_dlt = 4.0f * g.il * y * fmaf(2.0f * t, t, 1.0f) * Dy * c2i;    // 2 * delta
-    float alpha = -2.0f * g.iz * y * c2i;                                     // aCb slope in u
-    float beta = 4.0f * g.il * y * t * Dy * c2i;                              // aCb at u = 0
-    float gam2 = -4.0f * g.iz * y * t * c2i;                                  // 2 oCb slope in u
-    float Qu0 = aCa + two_dlt + gam2 * u0;
-    float dQ = gam2 * g.dz;
+    const float y2 = y * y;
+    const float aCa = 2.0f * g.iz * (g.R * g.R + y2) * c2i * c2i + 4.0f * g.il * y2 * t * t * c2i;
+    const float two_dlt = 4.0f * g.il * y * fmaf(2.0f * t, t, 1.0f) * Dy * c2i;   // 2 * delta
+    const float alpha = -2.0f * g.iz * y * c2i;                                    // aCb slope in u
+    const float beta = 4.0f * g.il * y * t * Dy * c2i;                             // aCb at u = 0
+    const float gam2 = -4.0f * g.iz * y * t * c2i;                                 // 2 oCb slope
+    const float Qc = aCa + two_dlt;                                                // Q at u = 0
     // Reading R5: P = 0 where Q <= 0.  Q is linear along the chord, so the
     // pixels with Q > 0 form a sub-range; keep only that.
-    float Qlast = fmaf((float)(len - 1), dQ, Qu0);
-    if (!(Qu0 > 0.0f && Qlast > 0.0f)) {
-        int mlo = 0, mhi = len - 1;
-        if (dQ > 0.0f && !(Qu0 > 0.0f))
-            mlo = (int)fminf(floorf(-Qu0 / dQ) + 1.0f, (float)len);
-        if (dQ < 0.0f && !(Qlast > 0.0f))
-            mhi = (int)fmaxf(fminf(ceilf(-Qu0 / dQ) - 1.0f, (float)len), -1.0f);
-        if (dQ == 0.0f) mhi = -1;
-        mlo = max(mlo, 0);
-        mhi = min(mhi, len - 1);
-        int keep = max(mhi - mlo + 1, 0);
-        qclip += (unsigned)(len - keep);
-        if (keep == 0) return;
-        lo += mlo;
-        len = keep;
-        u0 = fmaf((float)mlo, g.dz, u0);
-        Qu0 = fmaf((float)mlo, dQ, Qu0);
+    {
+        const float ulo = fmaf((float)lo, g.dz, g.z0) - c.zc;
+        const float uhi = fmaf((float)hi, g.dz, g.z0) - c.zc;
+        const float Qlo = fmaf(gam2, ulo, Qc), Qhi = fmaf(gam2, uhi, Qc);
+        if (!(Qlo > 0.0f && Qhi > 0.0f)) {
+            const int n0 = hi - lo + 1;
+            const float dQ = gam2 * g.dz;
+            int mlo = 0, mhi = n0 - 1;
+            if (dQ > 0.0f && !(Qlo > 0.0f))
+                mlo = (int)fminf(floorf(-Qlo / dQ) + 1.0f, (float)n0);
+            if (dQ < 0.0f && !(Qhi > 0.0f))
+                mhi = (int)fmaxf(fminf(ceilf(-Qlo / dQ) - 1.0f, (float)n0), -1.0f);
+            if (dQ == 0.0f) mhi = -1;
+            mlo = max(mlo, 0);
+            mhi = min(mhi, n0 - 1);
+            const int keep = max(mhi - mlo + 1, 0);
+            qclip += (unsigned)(n0 - keep);
+            if (keep == 0) return;
+            hi = lo + mhi;
+            lo = lo + mlo;
+        }
     }
-    r.len = len;
-    r.sbase = (iy - oy) * stride + (lo - oz);
-    r.Q0 = Qu0;
-    r.dQ = dQ;
+    const int cc = (lo + hi) >> 1;                   // chord centre column
+    // With the centre at (lo + hi) / 2 the right part has as many pixels as the
+    // left part or one more, so kAlt's first len steps cover exactly [lo, hi].
+    if (TRAV == kAlt) r.len = hi - lo + 1;
+    else if (TRAV == kPos) r.len = hi - cc + 1;
+    else r.len = cc - lo;
+    if (r.len <= 0) {
+        r.len = 0;
+        return;
+    }
+    const float u0 = fmaf((float)cc, g.dz, g.z0) - c.zc;
+    const int sidx = (iy - f.oy) * f.stride + (cc - z0row);
+    if (SMEM)
+        r.sbase = (unsigned)__cvta_generic_to_shared(base) + 4u * (unsigned)sidx;
+    else
+        r.gbase = (unsigned long long)(base + sidx);
+    r.Q0 = fmaf(gam2, u0, Qc);
+    r.dQ = gam2 * g.dz;
     r.A0 = g.kA * fmaf(alpha, u0, beta);
     r.dA = g.kA * alpha * g.dz;
     r.su0 = g.ksu * u0;
@@ -131,13 +178,13 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const d
         // Q = iz Qz + il Ql with Qz = 2 (R^2 + y^2) c2i^2 - 4 y t c2i u and
         // Ql = 4 y^2 t^2 c2i + 4 y (1 + 2 t^2) Dy c2i; aCb = iz Cz + il Cl with
         // Cz = -2 y c2i u, Cl = 4 y t Dy c2i; bCb = iz 2u^2 + il Bl, Bl = 4 Dy^2 c2i.
-        float qzc = (g.R * g.R + y2) * c2i * c2i;                     // Qz/2 at u = 0
-        float qzs = -2.0f * y * t * c2i;                               // (Qz/2) slope
+        const float qzc = (g.R * g.R + y2) * c2i * c2i;                 // Qz/2 at u = 0
+        const float qzs = -2.0f * y * t * c2i;                           // (Qz/2) slope
         rg.qz0 = fmaf(qzs, u0, qzc);
         rg.dqz = qzs * g.dz;
         rg.cz0 = -2.0f * y * c2i * u0;
         rg.dcz = -2.0f * y * c2i * g.dz;
-        float Bl = 4.0f * Dy * Dy * c2i;
+        const float Bl = 4.0f * Dy * Dy * c2i;
         rg.kz = 1.0f / g.iz;
         rg.kl = 0.5f / g.il - 0.5f * Bl;
         rg.cl = 4.0f * y * t * Dy * c2i;
@@ -145,61 +192,113 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const d
     }
 }
 
-// Pass 1 over the lane's chord: P[m] for m < len (values beyond len are
-// unspecified), the partial denominator sum P rho', and in GRAD mode the
-// partial sums of rho' P dlogP/d(iz) and rho' P dlogP/d(il).  rp points at the
-// lane's first pixel (reads up to LMAX-1 floats past the chord end must stay
-// inside the buffer; callers pad it).
-template <int LMAX, bool GRAD>
-__device__ __forceinline__ void pass1(const RowK& r, const RowG& rg, const float* rp, int maxlen,
-                                      float (&P)[LMAX], float& Dp, float& Ez, float& El)
+// Predicated load of rho' and accumulation of the denominator: if (m < len)
+// { v = mem[base + OFF]; D += p * v; } else v = 0.  Inactive lanes touch no
+// memory.
+template <bool SMEM, int OFF>
+__device__ __forceinline__ float load_acc(const RowK& r, int m, float p, float& D)
 {
-#pragma unroll
-    for (int m = 0; m < LMAX; ++m) {
-        if ((m & 3) == 0 && m >= maxlen) break;
-        const float fm = (float)m;
-        float Q = fmaf(fm, r.dQ, r.Q0);
-        float rq = rsqrt_approx(Q);
-        float su = fmaf(fm, r.dsu, r.su0);
-        float Aw = fmaf(fm, r.dA, r.A0);
-        float w = Aw * rq;
-        float arg = fmaf(w, w, fmaf(-su, su, r.C0));
-        float p = rq * ex2_approx(arg);
-        P[m] = p;
-        float rhop = rp[m];
-        bool on = m < r.len;
-        if (on) Dp = fmaf(p, rhop, Dp);
-        if (GRAD) {
+    float v;
+    if (SMEM) {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\t"
+            "setp.lt.s32 q, %2, %3;\n\t"
+            "mov.b32 %0, 0;\n\t"
+            "@q ld.shared.f32 %0, [%4+%5];\n\t"
+            "@q fma.rn.f32 %1, %6, %0, %1;\n\t}"
+            : "=&f"(v), "+f"(D)
+            : "r"(m), "r"(r.len), "r"(r.sbase), "n"(OFF), "f"(p));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\t"
+            "setp.lt.s32 q, %2, %3;\n\t"
+            "mov.b32 %0, 0;\n\t"
+            "@q ld.global.f32 %0, [%4+%5];\n\t"
+            "@q fma.rn.f32 %1, %6, %0, %1;\n\t}"
+            : "=&f"(v), "+f"(D)
+            : "r"(m), "r"(r.len), "l"(r.gbase), "n"(OFF), "f"(p));
+    }
+    return v;
+}
+
+// Predicated reduction: if (m < len) mem[base + OFF] += v.
+template <bool SMEM, int OFF>
+__device__ __forceinline__ void red_add(const RowK& r, int m, float v)
+{
+    if (SMEM) {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\t"
+            "setp.lt.s32 q, %0, %1;\n\t"
+            "@q red.shared.add.f32 [%2+%3], %4;\n\t}" ::"r"(m),
+            "r"(r.len), "r"(r.sbase), "n"(OFF), "f"(v)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\t"
+            "setp.lt.s32 q, %0, %1;\n\t"
+            "@q red.global.add.f32 [%2+%3], %4;\n\t}" ::"r"(m),
+            "r"(r.len), "l"(r.gbase), "n"(OFF), "f"(v)
+            : "memory");
+    }
+}
+
+// Pass 1, step M (template recursion so that each step's address offset is a
+// compile-time immediate).  P[M] holds the kernel value for M < len (values
+// beyond len are unspecified); Dp the partial denominator; in GRAD mode Ez, El
+// the partial sums of rho' P dlogP/d(iz) and rho' P dlogP/d(il).
+template <int TRAV, int LMAX, bool GRAD, bool SMEM, int M>
+__device__ __forceinline__ void pass1_step(const RowK& r, const RowG& rg, int maxlen,
+                                           float (&P)[LMAX], float& Dp, float& Ez, float& El)
+{
+    if constexpr (M < LMAX) {
+        if constexpr ((M & 3) == 0) {
+            if (M >= maxlen) return;
+        }
+        constexpr int d = trav_delta<TRAV>(M);
+        const float fd = (float)d;
+        const float Q = fmaf(fd, r.dQ, r.Q0);
+        const float rq = rsqrt_approx(Q);
+        const float su = fmaf(fd, r.dsu, r.su0);
+        const float Aw = fmaf(fd, r.dA, r.A0);
+        const float w = Aw * rq;
+        const float arg = fmaf(w, w, fmaf(-su, su, r.C0));
+        const float p = rq * ex2_approx(arg);
+        P[M] = p;
+        const float rhop = load_acc<SMEM, 4 * d>(r, M, p, Dp);
+        if constexpr (GRAD) {
             // d log P / d iz = 1/iz - u^2 + X Cz - (Qz/2)(1/Q + X^2)
             // d log P / d il = 1/(2 il) - Bl/2 + X Cl - (Ql/2)(1/Q + X^2)
             // with X = aCb / Q.
-            float u = fmaf(fm, rg.du, rg.u0);
-            float aCb = fmaf(fm, rg.db, rg.b0);
-            float iq = rq * rq;
-            float X = aCb * iq;
-            float S = fmaf(X, X, iq);
-            float qzh = fmaf(fm, rg.dqz, rg.qz0);
-            float cz = fmaf(fm, rg.dcz, rg.cz0);
-            float dz_ = fmaf(-qzh, S, fmaf(X, cz, fmaf(-u, u, rg.kz)));
-            float dl_ = fmaf(-rg.qlh, S, fmaf(X, rg.cl, rg.kl));
-            if (on) {
+            const float u = fmaf(fd, rg.du, rg.u0);
+            const float aCb = fmaf(fd, rg.db, rg.b0);
+            const float iq = rq * rq;
+            const float X = aCb * iq;
+            const float S = fmaf(X, X, iq);
+            const float qzh = fmaf(fd, rg.dqz, rg.qz0);
+            const float cz = fmaf(fd, rg.dcz, rg.cz0);
+            const float dz_ = fmaf(-qzh, S, fmaf(X, cz, fmaf(-u, u, rg.kz)));
+            const float dl_ = fmaf(-rg.qlh, S, fmaf(X, rg.cl, rg.kl));
+            if (M < r.len) {
                 const float wgt = p * rhop;
                 Ez = fmaf(wgt, dz_, Ez);
                 El = fmaf(wgt, dl_, El);
             }
         }
+        pass1_step<TRAV, LMAX, GRAD, SMEM, M + 1>(r, rg, maxlen, P, Dp, Ez, El);
     }
 }
 
-// Pass 2: acc[m] += P[m] * invD for m < len.
-template <int LMAX>
-__device__ __forceinline__ void pass2(const RowK& r, float* acc, int maxlen, const float (&P)[LMAX],
-                                      float invD)
+// Pass 2, step M: acc[d(M)] += P[M] * invD for M < len.
+template <int TRAV, int LMAX, bool SMEM, int M>
+__device__ __forceinline__ void pass2_step(const RowK& r, int maxlen, const float (&P)[LMAX],
+                                           float invD)
 {
-#pragma unroll
-    for (int m = 0; m < LMAX; ++m) {
-        if ((m & 3) == 0 && m >= maxlen) break;
-        if (m < r.len) atomicAdd(acc + m, P[m] * invD);
+    if constexpr (M < LMAX) {
+        if constexpr ((M & 3) == 0) {
+            if (M >= maxlen) return;
+        }
+        red_add<SMEM, 4 * trav_delta<TRAV>(M)>(r, M, P[M] * invD);
+        pass2_step<TRAV, LMAX, SMEM, M + 1>(r, maxlen, P, invD);
     }
 }
 
@@ -208,42 +307,36 @@ struct LeaderSums {
     unsigned long long used;
 };
 
-// One event processed by a group of G warps.  Lane-row q = wig*32 + lane
-// covers image row rows.x + q / nseg, segment q % nseg.  part: 2*G floats of
-// shared scratch for the group's cross-warp reduction (double-buffered by
-// parity).  Returns nothing; leader lanes accumulate their sums.
-template <int LMAX, int MODE>
-__device__ __forceinline__ void process_event(const Geo& g, const EventsView& evs, int e, int G,
-                                              int nseg, int wig, int lane, int bar_id,
-                                              float* part, int& parity, const float* rp_base,
-                                              float* acc_base, int oy, int oz, int stride, int rh,
-                                              int rw, LeaderSums& ls, unsigned& qclip,
-                                              unsigned& lclip)
+// One event processed by a group of G warps; the lane holds row rows.x + rowi
+// with traversal TRAV.  part: 6*G floats of shared scratch for the group's
+// cross-warp reduction (double-buffered by parity).
+template <int TRAV, int LMAX, int MODE, bool SMEM>
+__device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, int e, int rowi,
+                                           const Frame& f, const float* rp_base, float* acc_base,
+                                           int G, int wig, int lane, int bar_id, float* part,
+                                           int& parity, LeaderSums& ls, unsigned& qclip,
+                                           unsigned& lclip)
 {
     constexpr bool GRAD = (MODE == kGrad);
     const float4 ev = evs.geo[e];
     const int2 rws = evs.rows[e];
-    const int q = wig * 32 + lane;
-    const int rowi = q / nseg;
-    const int seg = q - rowi * nseg;
     RowK r;
     RowG rg;
     if (rowi < rws.y)
-        make_row<LMAX, GRAD>(g, ev, evs.geo64 + e, rws.x + rowi, seg, oy, oz, stride, rh, rw, r,
-                             rg, qclip, lclip);
+        make_row<TRAV, GRAD, SMEM>(g, ev, evs.geo64 + e, rws.x + rowi, f, rp_base, r, rg, qclip,
+                                   lclip);
     else
         row_idle<GRAD>(r, rg);
-    const int maxlen = __reduce_max_sync(0xffffffffu, (unsigned)r.len);
+    const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)r.len);
     float P[LMAX];
     float Dp = 0.0f, Ez = 0.0f, El = 0.0f;
-    pass1<LMAX, GRAD>(r, rg, rp_base + r.sbase, maxlen, P, Dp, Ez, El);
+    pass1_step<TRAV, LMAX, GRAD, SMEM, 0>(r, rg, maxlen, P, Dp, Ez, El);
     float D = warp_sum(Dp);
     if (GRAD) {
         Ez = warp_sum(Ez);
         El = warp_sum(El);
     }
     if (G > 1) {
-        const int nv = GRAD ? 3 : 1;
         float* slot = part + parity * (3 * G);
         if (lane == 0) {
             slot[wig] = D;
@@ -258,7 +351,7 @@ __device__ __forceinline__ void process_event(const Geo& g, const EventsView& ev
         El = 0.0f;
         for (int w = 0; w < G; ++w) {
             D += slot[w];
-            if (nv > 1) {
+            if (GRAD) {
                 Ez += slot[G + w];
                 El += slot[2 * G + w];
             }
@@ -275,9 +368,39 @@ __device__ __forceinline__ void process_event(const Geo& g, const EventsView& ev
             }
         }
         if (MODE != kLoglik) {
-            const float invD = 1.0f / D;
-            pass2<LMAX>(r, acc_base + r.sbase, maxlen, P, invD);
+            // the accumulator has the rho' buffer's layout at a fixed byte offset
+            RowK ra = r;
+            if (SMEM)
+                ra.sbase = r.sbase + (unsigned)((const char*)acc_base - (const char*)rp_base);
+            else
+                ra.gbase = r.gbase + (unsigned long long)((const char*)acc_base -
+                                                          (const char*)rp_base);
+            pass2_step<TRAV, LMAX, SMEM, 0>(ra, maxlen, P, 1.0f / D);
         }
+    }
+}
+
+// With nseg = 1 lane-row q = wig*32 + lane covers its row whole (kAlt); with
+// nseg = 2 even warps cover the right halves and odd warps the left halves of
+// rows (wig/2)*32 + lane (warp-uniform choice, no divergence).
+template <int LMAX, int MODE, bool SMEM>
+__device__ __forceinline__ void process_event(const Geo& g, const EventsView& evs, int e, int G,
+                                              int nseg, int wig, int lane, int bar_id,
+                                              float* part, int& parity, const Frame& f,
+                                              const float* rp_base, float* acc_base,
+                                              LeaderSums& ls, unsigned& qclip, unsigned& lclip)
+{
+    if (nseg == 1) {
+        event_rows<kAlt, LMAX, MODE, SMEM>(g, evs, e, wig * 32 + lane, f, rp_base, acc_base, G,
+                                          wig, lane, bar_id, part, parity, ls, qclip, lclip);
+    } else if ((wig & 1) == 0) {
+        event_rows<kPos, LMAX, MODE, SMEM>(g, evs, e, (wig >> 1) * 32 + lane, f, rp_base,
+                                          acc_base, G, wig, lane, bar_id, part, parity, ls, qclip,
+                                          lclip);
+    } else {
+        event_rows<kNeg, LMAX, MODE, SMEM>(g, evs, e, (wig >> 1) * 32 + lane, f, rp_base,
+                                          acc_base, G, wig, lane, bar_id, part, parity, ls, qclip,
+                                          lclip);
     }
 }
 
@@ -294,18 +417,16 @@ __device__ __forceinline__ void flush_leader_sums(const LeaderSums& ls, unsigned
     if (qclip) atomicAdd(&accum->n_qclip, (unsigned long long)qclip);
 }
 
-// Persistent tile kernel.  Shared memory: rho' region, accumulator region
-// (each RH*RS floats), then kPadFloats of slack, then the groups' reduction
-// slots (kWarps/G groups x 2 parities x 3G floats).
+// Persistent tile kernel.
 template <int LMAX, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tiles(Geo g, Tiling tl, EventsView evs, const int4* __restrict__ items, int n_items,
         const float* __restrict__ rhop, float* __restrict__ A, Accum* accum, int G, int nseg)
 {
     extern __shared__ float4 smem_f4[];
-    float* s_rp = reinterpret_cast<float*>(smem_f4);
+    float* s_rp = reinterpret_cast<float*>(smem_f4) + kPadFloats;
     const int region = tl.RH * tl.RS;
-    float* s_acc = s_rp + region;
+    float* s_acc = s_rp + region + 2 * kPadFloats;
     float* s_part = s_acc + region + kPadFloats;
     __shared__ int s_item;
 
@@ -317,22 +438,37 @@ k_tiles(Geo g, Tiling tl, EventsView evs, const int4* __restrict__ items, int n_
     LeaderSums ls = {0.0, 0.0, 0.0, 0ull};
     unsigned qclip = 0, lclip = 0;
 
-    // slack after the accumulator: finite values for reads past chord ends
-    for (int k = tid; k < kPadFloats; k += kThreads) s_acc[region + k] = 0.0f;
+    for (int k = tid; k < kPadFloats; k += kThreads) {
+        s_rp[-kPadFloats + k] = 0.0f;
+        s_rp[region + k] = 0.0f;
+        s_acc[-kPadFloats + k] = 0.0f;
+        s_acc[region + k] = 0.0f;
+    }
 
+    const int tiles_per_bin = tl.tiles_y * tl.tiles_z;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(&accum->queue, 1);
         __syncthreads();
         const int it = s_item;
         if (it >= n_items) break;
-        const int4 item = items[it];                // (tile, first event, count, 0)
-        const int ty = item.x / tl.tiles_z, tz = item.x - (item.x / tl.tiles_z) * tl.tiles_z;
-        const int oy = ty * tl.TY - tl.HY, oz = tz * tl.TZ - tl.HZ;
+        const int4 item = items[it];                // (bin, first event, count, 0)
+        const int b = item.x / tiles_per_bin;
+        const int rest = item.x - b * tiles_per_bin;
+        const int ty = rest / tl.tiles_z, tz = rest - (rest / tl.tiles_z) * tl.tiles_z;
+        Frame f;
+        f.oy = ty * tl.TY - tl.HY;
+        f.zbase = tz * tl.TZ - tl.HZ - tl.zs_off;
+        f.Y0 = tl.Y0;
+        f.stride = tl.RS;
+        f.rh = tl.RH;
+        f.rw = tl.RW;
+        f.shear = bin_shear(tl, b);
         for (int rr = warp; rr < tl.RH; rr += kWarps) {
-            const int iy = oy + rr;
+            const int iy = f.oy + rr;
             const bool row_in = iy >= 0 && iy < g.ny;
+            const int z0row = f.zbase + (int)rintf(__fmul_rn(f.shear, (float)(iy - f.Y0)));
             for (int cc = lane; cc < tl.RS; cc += 32) {
-                const int iz = oz + cc;
+                const int iz = z0row + cc;
                 float v = 0.0f;
                 if (row_in && cc < tl.RW && iz >= 0 && iz < g.nz) v = rhop[(size_t)iy * g.nz + iz];
                 s_rp[rr * tl.RS + cc] = v;
@@ -342,17 +478,17 @@ k_tiles(Geo g, Tiling tl, EventsView evs, const int4* __restrict__ items, int n_
         __syncthreads();
         if (grp < ngroups) {
             for (int e = item.y + grp; e < item.y + item.z; e += ngroups)
-                process_event<LMAX, MODE>(g, evs, e, G, nseg, wig, lane, 1 + grp, part, parity,
-                                          s_rp, s_acc, oy, oz, tl.RS, tl.RH, tl.RW, ls, qclip,
-                                          lclip);
+                process_event<LMAX, MODE, true>(g, evs, e, G, nseg, wig, lane, 1 + grp, part,
+                                                parity, f, s_rp, s_acc, ls, qclip, lclip);
         }
         __syncthreads();
         if (MODE != kLoglik) {
             for (int rr = warp; rr < tl.RH; rr += kWarps) {
-                const int iy = oy + rr;
+                const int iy = f.oy + rr;
                 if (iy < 0 || iy >= g.ny) continue;
+                const int z0row = f.zbase + (int)rintf(__fmul_rn(f.shear, (float)(iy - f.Y0)));
                 for (int cc = lane; cc < tl.RW; cc += 32) {
-                    const int iz = oz + cc;
+                    const int iz = z0row + cc;
                     const float v = s_acc[rr * tl.RS + cc];
                     if (iz >= 0 && iz < g.nz && v != 0.0f) atomicAdd(A + (size_t)iy * g.nz + iz, v);
                 }
@@ -363,7 +499,7 @@ k_tiles(Geo g, Tiling tl, EventsView evs, const int4* __restrict__ items, int n_
     flush_leader_sums(ls, qclip, lclip, accum, MODE);
 }
 
-// Events whose window does not fit their tile's halo: same evaluation, with
+// Events whose window does not fit their tile's region: same evaluation, with
 // rho' read from global memory and the scatter done by global atomics.
 template <int LMAX, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -378,10 +514,18 @@ k_outliers(Geo g, EventsView evs, int first, int count, const float* __restrict_
     int parity = 0;
     LeaderSums ls = {0.0, 0.0, 0.0, 0ull};
     unsigned qclip = 0, lclip = 0;
+    Frame f;
+    f.oy = 0;
+    f.zbase = 0;
+    f.Y0 = 0;
+    f.stride = g.nz;
+    f.rh = g.ny;
+    f.rw = g.nz;
+    f.shear = 0.0f;
     if (grp < ngroups) {
         for (int k = blockIdx.x * ngroups + grp; k < count; k += gridDim.x * ngroups)
-            process_event<LMAX, MODE>(g, evs, first + k, G, nseg, wig, lane, 1 + grp, part,
-                                      parity, rhop, A, 0, 0, g.nz, g.ny, g.nz, ls, qclip, lclip);
+            process_event<LMAX, MODE, false>(g, evs, first + k, G, nseg, wig, lane, 1 + grp, part,
+                                             parity, f, rhop, A, ls, qclip, lclip);
     }
     flush_leader_sums(ls, qclip, lclip, accum, MODE);
 }
