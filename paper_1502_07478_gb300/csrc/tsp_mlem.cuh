@@ -28,6 +28,8 @@
 // shared memory first.
 #pragma once
 
+#include <type_traits>
+
 #include "tsp_device.cuh"
 
 namespace tsp {
@@ -60,11 +62,19 @@ struct Frame {
 //   P = Q^(-1/2) 2^(C0 - s^2 + A^2/Q),  C0 = log2 K - (log2e/2) 4 il Dy^2 c2i,
 // K = det^(1/2)(C^-1) / (2 pi^2) (reading R4).  sbase / gbase is the byte
 // address of pixel c in the shared window or in the global image.
+template <bool SMEM>
 struct RowK {
     int len;
-    unsigned sbase;
-    unsigned long long gbase;
+    typename std::conditional<SMEM, unsigned, unsigned long long>::type base;
     float Q0, dQ, A0, dA, su0, dsu, C0;
+};
+
+// Per-block counters kept in shared memory (registers are the scarce resource
+// of the hot loop): events used, sum of log D, the sigma-gradient sums, and the
+// pixels dropped by reading R5 (Q <= 0) or by the region clamp.
+struct BlockSums {
+    unsigned long long used, qclip, lclip, pad;
+    double logD, giz, gil, pad2;
 };
 
 // Extra row constants of the sigma-gradient (adjoint) pass:
@@ -77,12 +87,11 @@ struct RowG {
 
 // An idle lane: no pixels, and constants that keep its (discarded) pass-1
 // arithmetic finite.
-template <bool GRAD>
-__device__ __forceinline__ void row_idle(RowK& r, RowG& rg)
+template <bool GRAD, bool SMEM>
+__device__ __forceinline__ void row_idle(RowK<SMEM>& r, RowG& rg)
 {
     r.len = 0;
-    r.sbase = 0;
-    r.gbase = 0;
+    r.base = 0;
     r.Q0 = 1.0f; r.dQ = 0.0f; r.A0 = 0.0f; r.dA = 0.0f; r.su0 = 0.0f; r.dsu = 0.0f;
     r.C0 = -126.0f;
     if (GRAD) {
@@ -96,21 +105,22 @@ __device__ __forceinline__ void row_idle(RowK& r, RowG& rg)
 // access in bounds regardless (clipped pixels are counted).
 template <int TRAV, bool GRAD, bool SMEM>
 __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const double4* ev64,
-                                         int iy, const Frame& f, const float* base, RowK& r,
-                                         RowG& rg, unsigned& qclip, unsigned& lclip)
+                                         int iy, const Frame* fp, const float* base,
+                                         RowK<SMEM>& r, RowG& rg, BlockSums* bs)
 {
-    row_idle<GRAD>(r, rg);
+    row_idle<GRAD, SMEM>(r, rg);
     const Chord c = row_chord(g, ev, ev64, iy);
     if (c.count <= 0) return;
+    const Frame f = *fp;
     int lo = c.lo, hi = c.lo + c.count - 1;
     if (iy < f.oy || iy >= f.oy + f.rh) {
-        lclip += (unsigned)c.count;
+        atomicAdd(&bs->lclip, (unsigned long long)c.count);
         return;
     }
     const int z0row = f.zbase + (int)rintf(__fmul_rn(f.shear, (float)(iy - f.Y0)));
     if (lo < z0row || hi >= z0row + f.rw) {
         const int lo2 = max(lo, z0row), hi2 = min(hi, z0row + f.rw - 1);
-        lclip += (unsigned)(c.count - max(hi2 - lo2 + 1, 0));
+        atomicAdd(&bs->lclip, (unsigned long long)(c.count - max(hi2 - lo2 + 1, 0)));
         lo = lo2;
         hi = hi2;
         if (hi < lo) return;
@@ -141,7 +151,7 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const d
             mlo = max(mlo, 0);
             mhi = min(mhi, n0 - 1);
             const int keep = max(mhi - mlo + 1, 0);
-            qclip += (unsigned)(n0 - keep);
+            atomicAdd(&bs->qclip, (unsigned long long)(n0 - keep));
             if (keep == 0) return;
             hi = lo + mhi;
             lo = lo + mlo;
@@ -159,10 +169,10 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const d
     }
     const float u0 = fmaf((float)cc, g.dz, g.z0) - c.zc;
     const int sidx = (iy - f.oy) * f.stride + (cc - z0row);
-    if (SMEM)
-        r.sbase = (unsigned)__cvta_generic_to_shared(base) + 4u * (unsigned)sidx;
+    if constexpr (SMEM)
+        r.base = (unsigned)__cvta_generic_to_shared(base) + 4u * (unsigned)sidx;
     else
-        r.gbase = (unsigned long long)(base + sidx);
+        r.base = (unsigned long long)(base + sidx);
     r.Q0 = fmaf(gam2, u0, Qc);
     r.dQ = gam2 * g.dz;
     r.A0 = g.kA * fmaf(alpha, u0, beta);
@@ -196,48 +206,48 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const d
 // { v = mem[base + OFF]; D += p * v; } else v = 0.  Inactive lanes touch no
 // memory.
 template <bool SMEM, int OFF>
-__device__ __forceinline__ float load_acc(const RowK& r, int m, float p, float& D)
+__device__ __forceinline__ float load_acc(const RowK<SMEM>& r, int m, float p, float& D)
 {
     float v;
-    if (SMEM) {
-        asm volatile(
+    if constexpr (SMEM) {
+        asm(
             "{\n\t.reg .pred q;\n\t"
             "setp.lt.s32 q, %2, %3;\n\t"
             "mov.b32 %0, 0;\n\t"
             "@q ld.shared.f32 %0, [%4+%5];\n\t"
             "@q fma.rn.f32 %1, %6, %0, %1;\n\t}"
             : "=&f"(v), "+f"(D)
-            : "r"(m), "r"(r.len), "r"(r.sbase), "n"(OFF), "f"(p));
+            : "r"(m), "r"(r.len), "r"(r.base), "n"(OFF), "f"(p));
     } else {
-        asm volatile(
+        asm(
             "{\n\t.reg .pred q;\n\t"
             "setp.lt.s32 q, %2, %3;\n\t"
             "mov.b32 %0, 0;\n\t"
             "@q ld.global.f32 %0, [%4+%5];\n\t"
             "@q fma.rn.f32 %1, %6, %0, %1;\n\t}"
             : "=&f"(v), "+f"(D)
-            : "r"(m), "r"(r.len), "l"(r.gbase), "n"(OFF), "f"(p));
+            : "r"(m), "r"(r.len), "l"(r.base), "n"(OFF), "f"(p));
     }
     return v;
 }
 
 // Predicated reduction: if (m < len) mem[base + OFF] += v.
 template <bool SMEM, int OFF>
-__device__ __forceinline__ void red_add(const RowK& r, int m, float v)
+__device__ __forceinline__ void red_add(const RowK<SMEM>& r, int m, float v)
 {
-    if (SMEM) {
+    if constexpr (SMEM) {
         asm volatile(
             "{\n\t.reg .pred q;\n\t"
             "setp.lt.s32 q, %0, %1;\n\t"
             "@q red.shared.add.f32 [%2+%3], %4;\n\t}" ::"r"(m),
-            "r"(r.len), "r"(r.sbase), "n"(OFF), "f"(v)
+            "r"(r.len), "r"(r.base), "n"(OFF), "f"(v)
             : "memory");
     } else {
         asm volatile(
             "{\n\t.reg .pred q;\n\t"
             "setp.lt.s32 q, %0, %1;\n\t"
             "@q red.global.add.f32 [%2+%3], %4;\n\t}" ::"r"(m),
-            "r"(r.len), "l"(r.gbase), "n"(OFF), "f"(v)
+            "r"(r.len), "l"(r.base), "n"(OFF), "f"(v)
             : "memory");
     }
 }
@@ -247,7 +257,7 @@ __device__ __forceinline__ void red_add(const RowK& r, int m, float v)
 // beyond len are unspecified); Dp the partial denominator; in GRAD mode Ez, El
 // the partial sums of rho' P dlogP/d(iz) and rho' P dlogP/d(il).
 template <int TRAV, int LMAX, bool GRAD, bool SMEM, int M>
-__device__ __forceinline__ void pass1_step(const RowK& r, const RowG& rg, int maxlen,
+__device__ __forceinline__ void pass1_step(const RowK<SMEM>& r, const RowG& rg, int maxlen,
                                            float (&P)[LMAX], float& Dp, float& Ez, float& El)
 {
     if constexpr (M < LMAX) {
@@ -290,7 +300,7 @@ __device__ __forceinline__ void pass1_step(const RowK& r, const RowG& rg, int ma
 
 // Pass 2, step M: acc[d(M)] += P[M] * invD for M < len.
 template <int TRAV, int LMAX, bool SMEM, int M>
-__device__ __forceinline__ void pass2_step(const RowK& r, int maxlen, const float (&P)[LMAX],
+__device__ __forceinline__ void pass2_step(const RowK<SMEM>& r, int maxlen, const float (&P)[LMAX],
                                            float invD)
 {
     if constexpr (M < LMAX) {
@@ -302,31 +312,24 @@ __device__ __forceinline__ void pass2_step(const RowK& r, int maxlen, const floa
     }
 }
 
-struct LeaderSums {
-    double logD, giz, gil;
-    unsigned long long used;
-};
-
 // One event processed by a group of G warps; the lane holds row rows.x + rowi
 // with traversal TRAV.  part: 6*G floats of shared scratch for the group's
 // cross-warp reduction (double-buffered by parity).
 template <int TRAV, int LMAX, int MODE, bool SMEM>
 __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, int e, int rowi,
-                                           const Frame& f, const float* rp_base, float* acc_base,
+                                           const Frame* f, const float* rp_base, float* acc_base,
                                            int G, int wig, int lane, int bar_id, float* part,
-                                           int& parity, LeaderSums& ls, unsigned& qclip,
-                                           unsigned& lclip)
+                                           int& parity, BlockSums* bs)
 {
     constexpr bool GRAD = (MODE == kGrad);
     const float4 ev = evs.geo[e];
     const int2 rws = evs.rows[e];
-    RowK r;
+    RowK<SMEM> r;
     RowG rg;
     if (rowi < rws.y)
-        make_row<TRAV, GRAD, SMEM>(g, ev, evs.geo64 + e, rws.x + rowi, f, rp_base, r, rg, qclip,
-                                   lclip);
+        make_row<TRAV, GRAD, SMEM>(g, ev, evs.geo64 + e, rws.x + rowi, f, rp_base, r, rg, bs);
     else
-        row_idle<GRAD>(r, rg);
+        row_idle<GRAD, SMEM>(r, rg);
     const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)r.len);
     float P[LMAX];
     float Dp = 0.0f, Ez = 0.0f, El = 0.0f;
@@ -360,68 +363,70 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
     }
     if (D > 0.0f) {
         if (wig == 0 && lane == 0) {
-            ls.used += 1;
-            if (MODE != kMlem) ls.logD += (double)logf(D);
+            atomicAdd(&bs->used, 1ull);
+            if (MODE != kMlem) atomicAdd(&bs->logD, (double)logf(D));
             if (GRAD) {
-                ls.giz += (double)(Ez / D);
-                ls.gil += (double)(El / D);
+                atomicAdd(&bs->giz, (double)(Ez / D));
+                atomicAdd(&bs->gil, (double)(El / D));
             }
         }
         if (MODE != kLoglik) {
             // the accumulator has the rho' buffer's layout at a fixed byte offset
-            RowK ra = r;
-            if (SMEM)
-                ra.sbase = r.sbase + (unsigned)((const char*)acc_base - (const char*)rp_base);
-            else
-                ra.gbase = r.gbase + (unsigned long long)((const char*)acc_base -
-                                                          (const char*)rp_base);
+            RowK<SMEM> ra = r;
+            ra.base += (decltype(ra.base))((const char*)acc_base - (const char*)rp_base);
             pass2_step<TRAV, LMAX, SMEM, 0>(ra, maxlen, P, 1.0f / D);
         }
     }
 }
 
-// With nseg = 1 lane-row q = wig*32 + lane covers its row whole (kAlt); with
-// nseg = 2 even warps cover the right halves and odd warps the left halves of
-// rows (wig/2)*32 + lane (warp-uniform choice, no divergence).
-template <int LMAX, int MODE, bool SMEM>
+// NSEG = 1: lane-row q = wig*32 + lane covers its row whole (kAlt).  NSEG = 2:
+// even warps cover the right halves and odd warps the left halves of rows
+// (wig/2)*32 + lane (a warp-uniform choice, no divergence).
+template <int LMAX, int MODE, int NSEG, bool SMEM>
 __device__ __forceinline__ void process_event(const Geo& g, const EventsView& evs, int e, int G,
-                                              int nseg, int wig, int lane, int bar_id,
-                                              float* part, int& parity, const Frame& f,
-                                              const float* rp_base, float* acc_base,
-                                              LeaderSums& ls, unsigned& qclip, unsigned& lclip)
+                                              int wig, int lane, int bar_id, float* part,
+                                              int& parity, const Frame* f, const float* rp_base,
+                                              float* acc_base, BlockSums* bs)
 {
-    if (nseg == 1) {
+    if constexpr (NSEG == 1) {
         event_rows<kAlt, LMAX, MODE, SMEM>(g, evs, e, wig * 32 + lane, f, rp_base, acc_base, G,
-                                          wig, lane, bar_id, part, parity, ls, qclip, lclip);
-    } else if ((wig & 1) == 0) {
-        event_rows<kPos, LMAX, MODE, SMEM>(g, evs, e, (wig >> 1) * 32 + lane, f, rp_base,
-                                          acc_base, G, wig, lane, bar_id, part, parity, ls, qclip,
-                                          lclip);
+                                          wig, lane, bar_id, part, parity, bs);
     } else {
-        event_rows<kNeg, LMAX, MODE, SMEM>(g, evs, e, (wig >> 1) * 32 + lane, f, rp_base,
-                                          acc_base, G, wig, lane, bar_id, part, parity, ls, qclip,
-                                          lclip);
+        if ((wig & 1) == 0)
+            event_rows<kPos, LMAX, MODE, SMEM>(g, evs, e, (wig >> 1) * 32 + lane, f, rp_base,
+                                              acc_base, G, wig, lane, bar_id, part, parity, bs);
+        else
+            event_rows<kNeg, LMAX, MODE, SMEM>(g, evs, e, (wig >> 1) * 32 + lane, f, rp_base,
+                                              acc_base, G, wig, lane, bar_id, part, parity, bs);
     }
 }
 
-__device__ __forceinline__ void flush_leader_sums(const LeaderSums& ls, unsigned qclip,
-                                                  unsigned lclip, Accum* accum, int mode)
+__device__ __forceinline__ void init_block_sums(BlockSums* bs)
 {
-    if (ls.used) atomicAdd(&accum->n_used, ls.used);
-    if (lclip) atomicAdd(&accum->n_lclip, (unsigned long long)lclip);
-    if (mode != kMlem && ls.logD != 0.0) atomicAdd(&accum->sum_logD, ls.logD);
-    if (mode == kGrad) {
-        if (ls.giz != 0.0) atomicAdd(&accum->g_iz, ls.giz);
-        if (ls.gil != 0.0) atomicAdd(&accum->g_il, ls.gil);
+    if (threadIdx.x == 0) {
+        bs->used = bs->qclip = bs->lclip = 0ull;
+        bs->logD = bs->giz = bs->gil = 0.0;
     }
-    if (qclip) atomicAdd(&accum->n_qclip, (unsigned long long)qclip);
+}
+
+__device__ __forceinline__ void flush_block_sums(const BlockSums* bs, Accum* accum, int mode)
+{
+    if (threadIdx.x != 0) return;
+    if (bs->used) atomicAdd(&accum->n_used, bs->used);
+    if (bs->lclip) atomicAdd(&accum->n_lclip, bs->lclip);
+    if (bs->qclip) atomicAdd(&accum->n_qclip, bs->qclip);
+    if (mode != kMlem && bs->logD != 0.0) atomicAdd(&accum->sum_logD, bs->logD);
+    if (mode == kGrad) {
+        if (bs->giz != 0.0) atomicAdd(&accum->g_iz, bs->giz);
+        if (bs->gil != 0.0) atomicAdd(&accum->g_il, bs->gil);
+    }
 }
 
 // Persistent tile kernel.
-template <int LMAX, int MODE>
+template <int LMAX, int MODE, int NSEG>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tiles(Geo g, Tiling tl, EventsView evs, const int4* __restrict__ items, int n_items,
-        const float* __restrict__ rhop, float* __restrict__ A, Accum* accum, int G, int nseg)
+        const float* __restrict__ rhop, float* __restrict__ A, Accum* accum, int G)
 {
     extern __shared__ float4 smem_f4[];
     float* s_rp = reinterpret_cast<float*>(smem_f4) + kPadFloats;
@@ -429,14 +434,15 @@ k_tiles(Geo g, Tiling tl, EventsView evs, const int4* __restrict__ items, int n_
     float* s_acc = s_rp + region + 2 * kPadFloats;
     float* s_part = s_acc + region + kPadFloats;
     __shared__ int s_item;
+    __shared__ Frame s_frame;
+    __shared__ BlockSums s_sums;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ngroups = kWarps / G;
     const int grp = warp / G, wig = warp - grp * G;
     float* part = s_part + grp * (2 * 3 * G);
     int parity = 0;
-    LeaderSums ls = {0.0, 0.0, 0.0, 0ull};
-    unsigned qclip = 0, lclip = 0;
+    init_block_sums(&s_sums);
 
     for (int k = tid; k < kPadFloats; k += kThreads) {
         s_rp[-kPadFloats + k] = 0.0f;
@@ -447,42 +453,52 @@ k_tiles(Geo g, Tiling tl, EventsView evs, const int4* __restrict__ items, int n_
 
     const int tiles_per_bin = tl.tiles_y * tl.tiles_z;
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(&accum->queue, 1);
+        if (tid == 0) {
+            const int it = atomicAdd(&accum->queue, 1);
+            s_item = it;
+            if (it < n_items) {
+                const int4 item = items[it];        // (bin, first event, count, 0)
+                const int b = item.x / tiles_per_bin;
+                const int rest = item.x - b * tiles_per_bin;
+                const int ty = rest / tl.tiles_z, tz = rest - (rest / tl.tiles_z) * tl.tiles_z;
+                s_frame.oy = ty * tl.TY - tl.HY;
+                s_frame.zbase = tz * tl.TZ - tl.HZ - tl.zs_off;
+                s_frame.Y0 = tl.Y0;
+                s_frame.stride = tl.RS;
+                s_frame.rh = tl.RH;
+                s_frame.rw = tl.RW;
+                s_frame.shear = bin_shear(tl, b);
+            }
+        }
         __syncthreads();
         const int it = s_item;
         if (it >= n_items) break;
-        const int4 item = items[it];                // (bin, first event, count, 0)
-        const int b = item.x / tiles_per_bin;
-        const int rest = item.x - b * tiles_per_bin;
-        const int ty = rest / tl.tiles_z, tz = rest - (rest / tl.tiles_z) * tl.tiles_z;
-        Frame f;
-        f.oy = ty * tl.TY - tl.HY;
-        f.zbase = tz * tl.TZ - tl.HZ - tl.zs_off;
-        f.Y0 = tl.Y0;
-        f.stride = tl.RS;
-        f.rh = tl.RH;
-        f.rw = tl.RW;
-        f.shear = bin_shear(tl, b);
-        for (int rr = warp; rr < tl.RH; rr += kWarps) {
-            const int iy = f.oy + rr;
-            const bool row_in = iy >= 0 && iy < g.ny;
-            const int z0row = f.zbase + (int)rintf(__fmul_rn(f.shear, (float)(iy - f.Y0)));
-            for (int cc = lane; cc < tl.RS; cc += 32) {
-                const int iz = z0row + cc;
-                float v = 0.0f;
-                if (row_in && cc < tl.RW && iz >= 0 && iz < g.nz) v = rhop[(size_t)iy * g.nz + iz];
-                s_rp[rr * tl.RS + cc] = v;
-                if (MODE != kLoglik) s_acc[rr * tl.RS + cc] = 0.0f;
+        const int4 item = items[it];
+        {
+            const Frame f = s_frame;
+            for (int rr = warp; rr < tl.RH; rr += kWarps) {
+                const int iy = f.oy + rr;
+                const bool row_in = iy >= 0 && iy < g.ny;
+                const int z0row = f.zbase + (int)rintf(__fmul_rn(f.shear, (float)(iy - f.Y0)));
+                for (int cc = lane; cc < tl.RS; cc += 32) {
+                    const int iz = z0row + cc;
+                    float v = 0.0f;
+                    if (row_in && cc < tl.RW && iz >= 0 && iz < g.nz)
+                        v = rhop[(size_t)iy * g.nz + iz];
+                    s_rp[rr * tl.RS + cc] = v;
+                    if (MODE != kLoglik) s_acc[rr * tl.RS + cc] = 0.0f;
+                }
             }
         }
         __syncthreads();
         if (grp < ngroups) {
             for (int e = item.y + grp; e < item.y + item.z; e += ngroups)
-                process_event<LMAX, MODE, true>(g, evs, e, G, nseg, wig, lane, 1 + grp, part,
-                                                parity, f, s_rp, s_acc, ls, qclip, lclip);
+                process_event<LMAX, MODE, NSEG, true>(g, evs, e, G, wig, lane, 1 + grp, part,
+                                                      parity, &s_frame, s_rp, s_acc, &s_sums);
         }
         __syncthreads();
         if (MODE != kLoglik) {
+            const Frame f = s_frame;
             for (int rr = warp; rr < tl.RH; rr += kWarps) {
                 const int iy = f.oy + rr;
                 if (iy < 0 || iy >= g.ny) continue;
@@ -496,38 +512,43 @@ k_tiles(Geo g, Tiling tl, EventsView evs, const int4* __restrict__ items, int n_
             __syncthreads();
         }
     }
-    flush_leader_sums(ls, qclip, lclip, accum, MODE);
+    __syncthreads();
+    flush_block_sums(&s_sums, accum, MODE);
 }
 
 // Events whose window does not fit their tile's region: same evaluation, with
 // rho' read from global memory and the scatter done by global atomics.
-template <int LMAX, int MODE>
+template <int LMAX, int MODE, int NSEG>
 __global__ void __launch_bounds__(kThreads, 1)
 k_outliers(Geo g, EventsView evs, int first, int count, const float* __restrict__ rhop,
-           float* __restrict__ A, Accum* accum, int G, int nseg)
+           float* __restrict__ A, Accum* accum, int G)
 {
     __shared__ float s_part[kWarps * 2 * 3];
+    __shared__ Frame s_frame;
+    __shared__ BlockSums s_sums;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ngroups = kWarps / G;
     const int grp = warp / G, wig = warp - grp * G;
     float* part = s_part + grp * (2 * 3 * G);
     int parity = 0;
-    LeaderSums ls = {0.0, 0.0, 0.0, 0ull};
-    unsigned qclip = 0, lclip = 0;
-    Frame f;
-    f.oy = 0;
-    f.zbase = 0;
-    f.Y0 = 0;
-    f.stride = g.nz;
-    f.rh = g.ny;
-    f.rw = g.nz;
-    f.shear = 0.0f;
+    init_block_sums(&s_sums);
+    if (tid == 0) {
+        s_frame.oy = 0;
+        s_frame.zbase = 0;
+        s_frame.Y0 = 0;
+        s_frame.stride = g.nz;
+        s_frame.rh = g.ny;
+        s_frame.rw = g.nz;
+        s_frame.shear = 0.0f;
+    }
+    __syncthreads();
     if (grp < ngroups) {
         for (int k = blockIdx.x * ngroups + grp; k < count; k += gridDim.x * ngroups)
-            process_event<LMAX, MODE, false>(g, evs, first + k, G, nseg, wig, lane, 1 + grp, part,
-                                             parity, f, rhop, A, ls, qclip, lclip);
+            process_event<LMAX, MODE, NSEG, false>(g, evs, first + k, G, wig, lane, 1 + grp, part,
+                                                   parity, &s_frame, rhop, A, &s_sums);
     }
-    flush_leader_sums(ls, qclip, lclip, accum, MODE);
+    __syncthreads();
+    flush_block_sums(&s_sums, accum, MODE);
 }
 
 }  // namespace tsp
