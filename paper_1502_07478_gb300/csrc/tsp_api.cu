@@ -13,7 +13,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/tsp.h"
+#include "tsp.h"
 #include "tsp_launch.h"
 
 using namespace tsp;
