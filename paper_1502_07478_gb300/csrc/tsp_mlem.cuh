@@ -54,17 +54,18 @@ struct Frame {
     float shear;
 };
 
-// Per-lane row constants, relative to the lane's chord centre c.  For step m
-// with d = trav_delta(m):
+// Per-lane row constants, relative to the lane's traversal origin c.  Step m
+// (d = trav_delta(m)) is inside the lane's chord iff m < lim_odd (m odd) or
+// m < lim_even (m even).  For step m with d = trav_delta(m):
 //   u = u0 + d dz,  Q = aCa + 2 oCb = Q0 + d dQ,
 //   A = sqrt(log2e/2) aCb = A0 + d dA,  s = sqrt(log2e iz) u = su0 + d dsu,
 // and Eq. kernel becomes
 //   P = Q^(-1/2) 2^(C0 - s^2 + A^2/Q),  C0 = log2 K - (log2e/2) 4 il Dy^2 c2i,
-// K = det^(1/2)(C^-1) / (2 pi^2) (reading R4).  sbase / gbase is the byte
-// address of pixel c in the shared window or in the global image.
+// K = det^(1/2)(C^-1) / (2 pi^2) (reading R4).  base is the byte address of
+// pixel c in the shared window (32-bit) or in the global image.
 template <bool SMEM>
 struct RowK {
-    int len;
+    int lim_odd, lim_even;
     typename std::conditional<SMEM, unsigned, unsigned long long>::type base;
     float Q0, dQ, A0, dA, su0, dsu, C0;
 };
@@ -90,7 +91,8 @@ struct RowG {
 template <bool GRAD, bool SMEM>
 __device__ __forceinline__ void row_idle(RowK<SMEM>& r, RowG& rg)
 {
-    r.len = 0;
+    r.lim_odd = 0;
+    r.lim_even = 0;
     r.base = 0;
     r.Q0 = 1.0f; r.dQ = 0.0f; r.A0 = 0.0f; r.dA = 0.0f; r.su0 = 0.0f; r.dsu = 0.0f;
     r.C0 = -126.0f;
@@ -100,75 +102,101 @@ __device__ __forceinline__ void row_idle(RowK<SMEM>& r, RowG& rg)
     }
 }
 
-// Row constants of lane row iy for the traversal TRAV.  The event preparation
-// guarantees that every chord lies inside the frame; the clamp keeps every
-// access in bounds regardless (clipped pixels are counted).
-template <int TRAV, bool GRAD, bool SMEM>
+// Row constants of lane row iy (valid_row = false for a lane without a row)
+// for the traversal TRAV.  All 32 lanes of the warp must call it together: the
+// lanes agree on one stored column (the middle of their chord centres) as
+// their common traversal origin, so that at every step neighbouring lanes
+// (neighbouring rows, row stride = 1 mod 32 words) address distinct banks.  A
+// lane whose chord does not contain that column starts at its own centre.
+// The event preparation guarantees that every chord lies inside the frame;
+// the clamp keeps every access in bounds regardless (clipped pixels are
+// counted).
+template <int TRAV, int LMAX, bool GRAD, bool SMEM>
 __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const double4* ev64,
-                                         int iy, const Frame* fp, const float* base,
-                                         RowK<SMEM>& r, RowG& rg, BlockSums* bs)
+                                         int iy, bool valid_row, const Frame* fp,
+                                         const float* base, RowK<SMEM>& r, RowG& rg,
+                                         BlockSums* bs)
 {
     row_idle<GRAD, SMEM>(r, rg);
-    const Chord c = row_chord(g, ev, ev64, iy);
-    if (c.count <= 0) return;
+    Chord c;
+    c.y = c.Dy = c.B0 = c.zc = 0.0f;
+    int lo = 0, hi = -1, z0row = 0;
     const Frame f = *fp;
-    int lo = c.lo, hi = c.lo + c.count - 1;
-    if (iy < f.oy || iy >= f.oy + f.rh) {
-        atomicAdd(&bs->lclip, (unsigned long long)c.count);
-        return;
-    }
-    const int z0row = f.zbase + (int)rintf(__fmul_rn(f.shear, (float)(iy - f.Y0)));
-    if (lo < z0row || hi >= z0row + f.rw) {
-        const int lo2 = max(lo, z0row), hi2 = min(hi, z0row + f.rw - 1);
-        atomicAdd(&bs->lclip, (unsigned long long)(c.count - max(hi2 - lo2 + 1, 0)));
-        lo = lo2;
-        hi = hi2;
-        if (hi < lo) return;
-    }
-    const float t = ev.z, c2i = ev.w, y = c.y, Dy = c.Dy;
-    const float y2 = y * y;
-    const float aCa = 2.0f * g.iz * (g.R * g.R + y2) * c2i * c2i + 4.0f * g.il * y2 * t * t * c2i;
-    const float two_dlt = 4.0f * g.il * y * fmaf(2.0f * t, t, 1.0f) * Dy * c2i;   // 2 * delta
-    const float alpha = -2.0f * g.iz * y * c2i;                                    // aCb slope in u
-    const float beta = 4.0f * g.il * y * t * Dy * c2i;                             // aCb at u = 0
-    const float gam2 = -4.0f * g.iz * y * t * c2i;                                 // 2 oCb slope
-    const float Qc = aCa + two_dlt;                                                // Q at u = 0
-    // Reading R5: P = 0 where Q <= 0.  Q is linear along the chord, so the
-    // pixels with Q > 0 form a sub-range; keep only that.
-    {
-        const float ulo = fmaf((float)lo, g.dz, g.z0) - c.zc;
-        const float uhi = fmaf((float)hi, g.dz, g.z0) - c.zc;
-        const float Qlo = fmaf(gam2, ulo, Qc), Qhi = fmaf(gam2, uhi, Qc);
-        if (!(Qlo > 0.0f && Qhi > 0.0f)) {
-            const int n0 = hi - lo + 1;
-            const float dQ = gam2 * g.dz;
-            int mlo = 0, mhi = n0 - 1;
-            if (dQ > 0.0f && !(Qlo > 0.0f))
-                mlo = (int)fminf(floorf(-Qlo / dQ) + 1.0f, (float)n0);
-            if (dQ < 0.0f && !(Qhi > 0.0f))
-                mhi = (int)fmaxf(fminf(ceilf(-Qlo / dQ) - 1.0f, (float)n0), -1.0f);
-            if (dQ == 0.0f) mhi = -1;
-            mlo = max(mlo, 0);
-            mhi = min(mhi, n0 - 1);
-            const int keep = max(mhi - mlo + 1, 0);
-            atomicAdd(&bs->qclip, (unsigned long long)(n0 - keep));
-            if (keep == 0) return;
-            hi = lo + mhi;
-            lo = lo + mlo;
+    float Qc = 0.0f, gam2 = 0.0f;
+    if (valid_row) {
+        c = row_chord(g, ev, ev64, iy);
+        lo = c.lo;
+        hi = c.lo + c.count - 1;
+        if (c.count > 0 && (iy < f.oy || iy >= f.oy + f.rh)) {
+            atomicAdd(&bs->lclip, (unsigned long long)c.count);
+            hi = lo - 1;
+        }
+        z0row = f.zbase + (int)rintf(__fmul_rn(f.shear, (float)(iy - f.Y0)));
+        if (hi >= lo && (lo < z0row || hi >= z0row + f.rw)) {
+            const int lo2 = max(lo, z0row), hi2 = min(hi, z0row + f.rw - 1);
+            atomicAdd(&bs->lclip, (unsigned long long)(c.count - max(hi2 - lo2 + 1, 0)));
+            lo = lo2;
+            hi = hi2;
+        }
+        if (hi >= lo) {
+            const float t = ev.z, c2i = ev.w, y = c.y, Dy = c.Dy, y2 = y * y;
+            const float aCa =
+                2.0f * g.iz * (g.R * g.R + y2) * c2i * c2i + 4.0f * g.il * y2 * t * t * c2i;
+            Qc = aCa + 4.0f * g.il * y * fmaf(2.0f * t, t, 1.0f) * Dy * c2i;   // Q at u = 0
+            gam2 = -4.0f * g.iz * y * t * c2i;                                 // 2 oCb slope
+            // Reading R5: P = 0 where Q <= 0.  Q is linear along the chord, so
+            // the pixels with Q > 0 form a sub-range; keep only that.
+            const float ulo = fmaf((float)lo, g.dz, g.z0) - c.zc;
+            const float uhi = fmaf((float)hi, g.dz, g.z0) - c.zc;
+            const float Qlo = fmaf(gam2, ulo, Qc), Qhi = fmaf(gam2, uhi, Qc);
+            if (!(Qlo > 0.0f && Qhi > 0.0f)) {
+                const int n0 = hi - lo + 1;
+                const float dQ = gam2 * g.dz;
+                int mlo = 0, mhi = n0 - 1;
+                if (dQ > 0.0f && !(Qlo > 0.0f))
+                    mlo = (int)fminf(floorf(-Qlo / dQ) + 1.0f, (float)n0);
+                if (dQ < 0.0f && !(Qhi > 0.0f))
+                    mhi = (int)fmaxf(fminf(ceilf(-Qlo / dQ) - 1.0f, (float)n0), -1.0f);
+                if (dQ == 0.0f) mhi = -1;
+                mlo = max(mlo, 0);
+                mhi = min(mhi, n0 - 1);
+                const int keep = max(mhi - mlo + 1, 0);
+                atomicAdd(&bs->qclip, (unsigned long long)(n0 - keep));
+                hi = lo + mhi;
+                lo = lo + mlo;
+            }
         }
     }
-    const int cc = (lo + hi) >> 1;                   // chord centre column
-    // With the centre at (lo + hi) / 2 the right part has as many pixels as the
-    // left part or one more, so kAlt's first len steps cover exactly [lo, hi].
-    if (TRAV == kAlt) r.len = hi - lo + 1;
-    else if (TRAV == kPos) r.len = hi - cc + 1;
-    else r.len = cc - lo;
-    if (r.len <= 0) {
-        r.len = 0;
-        return;
+    const bool has = hi >= lo;
+    const int sc = ((lo + hi) >> 1) - z0row;               // stored column of the centre
+    const int smin = __reduce_min_sync(0xffffffffu, has ? sc : 0x7fffffff);
+    const int smax = __reduce_max_sync(0xffffffffu, has ? sc : (int)0x80000000);
+    if (!has) return;
+    // The common origin is used only when it lies within 2 columns of the
+    // lane's own chord centre cc and keeps the lane's walk within LMAX steps;
+    // otherwise the lane starts at cc (then kAlt needs exactly hi - lo + 1 <=
+    // LMAX steps and each half of kPos / kNeg at most LMAX).
+    const int k0 = (int)(((long long)smin + (long long)smax) >> 1);
+    const int cc = (lo + hi) >> 1;
+    int o = k0 + z0row;
+    if (o < cc - 2 || o > cc + 2 || o < lo || o > hi) o = cc;
+    if (TRAV == kAlt && max(2 * (hi - o), 2 * (o - lo) + 1) > LMAX) o = cc;
+    if (TRAV == kPos && hi - o + 1 > LMAX) o = cc;
+    if (TRAV == kNeg && o - lo > LMAX) o = cc;
+    const int L = o - lo, R = hi - o;
+    if (TRAV == kAlt) {
+        r.lim_odd = 2 * R;          // odd m reach d = (m+1)/2 <= R
+        r.lim_even = 2 * L + 1;     // even m reach d = -m/2 >= -L
+    } else if (TRAV == kPos) {
+        r.lim_odd = r.lim_even = R + 1;
+    } else {
+        r.lim_odd = r.lim_even = L;
     }
-    const float u0 = fmaf((float)cc, g.dz, g.z0) - c.zc;
-    const int sidx = (iy - f.oy) * f.stride + (cc - z0row);
+    const float t = ev.z, c2i = ev.w, y = c.y, Dy = c.Dy;
+    const float alpha = -2.0f * g.iz * y * c2i;                                    // aCb slope in u
+    const float beta = 4.0f * g.il * y * t * Dy * c2i;                             // aCb at u = 0
+    const float u0 = fmaf((float)o, g.dz, g.z0) - c.zc;
+    const int sidx = (iy - f.oy) * f.stride + (o - z0row);
     if constexpr (SMEM)
         r.base = (unsigned)__cvta_generic_to_shared(base) + 4u * (unsigned)sidx;
     else
@@ -181,6 +209,7 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const d
     r.dsu = g.ksu * g.dz;
     r.C0 = g.log2K - g.half_log2e * c.B0;
     if (GRAD) {
+        const float y2 = y * y;
         rg.u0 = u0;
         rg.du = g.dz;
         rg.b0 = fmaf(alpha, u0, beta);
@@ -206,7 +235,7 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const d
 // { v = mem[base + OFF]; D += p * v; } else v = 0.  Inactive lanes touch no
 // memory.
 template <bool SMEM, int OFF>
-__device__ __forceinline__ float load_acc(const RowK<SMEM>& r, int m, float p, float& D)
+__device__ __forceinline__ float load_acc(const RowK<SMEM>& r, int lim, int m, float p, float& D)
 {
     float v;
     if constexpr (SMEM) {
@@ -217,7 +246,7 @@ __device__ __forceinline__ float load_acc(const RowK<SMEM>& r, int m, float p, f
             "@q ld.shared.f32 %0, [%4+%5];\n\t"
             "@q fma.rn.f32 %1, %6, %0, %1;\n\t}"
             : "=&f"(v), "+f"(D)
-            : "r"(m), "r"(r.len), "r"(r.base), "n"(OFF), "f"(p));
+            : "r"(m), "r"(lim), "r"(r.base), "n"(OFF), "f"(p));
     } else {
         asm(
             "{\n\t.reg .pred q;\n\t"
@@ -226,28 +255,28 @@ __device__ __forceinline__ float load_acc(const RowK<SMEM>& r, int m, float p, f
             "@q ld.global.f32 %0, [%4+%5];\n\t"
             "@q fma.rn.f32 %1, %6, %0, %1;\n\t}"
             : "=&f"(v), "+f"(D)
-            : "r"(m), "r"(r.len), "l"(r.base), "n"(OFF), "f"(p));
+            : "r"(m), "r"(lim), "l"(r.base), "n"(OFF), "f"(p));
     }
     return v;
 }
 
 // Predicated reduction: if (m < len) mem[base + OFF] += v.
 template <bool SMEM, int OFF>
-__device__ __forceinline__ void red_add(const RowK<SMEM>& r, int m, float v)
+__device__ __forceinline__ void red_add(const RowK<SMEM>& r, int lim, int m, float v)
 {
     if constexpr (SMEM) {
         asm volatile(
             "{\n\t.reg .pred q;\n\t"
             "setp.lt.s32 q, %0, %1;\n\t"
             "@q red.shared.add.f32 [%2+%3], %4;\n\t}" ::"r"(m),
-            "r"(r.len), "r"(r.base), "n"(OFF), "f"(v)
+            "r"(lim), "r"(r.base), "n"(OFF), "f"(v)
             : "memory");
     } else {
         asm volatile(
             "{\n\t.reg .pred q;\n\t"
             "setp.lt.s32 q, %0, %1;\n\t"
             "@q red.global.add.f32 [%2+%3], %4;\n\t}" ::"r"(m),
-            "r"(r.len), "l"(r.base), "n"(OFF), "f"(v)
+            "r"(lim), "l"(r.base), "n"(OFF), "f"(v)
             : "memory");
     }
 }
@@ -274,7 +303,8 @@ __device__ __forceinline__ void pass1_step(const RowK<SMEM>& r, const RowG& rg, 
         const float arg = fmaf(w, w, fmaf(-su, su, r.C0));
         const float p = rq * ex2_approx(arg);
         P[M] = p;
-        const float rhop = load_acc<SMEM, 4 * d>(r, M, p, Dp);
+        const int lim = (M & 1) ? r.lim_odd : r.lim_even;
+        const float rhop = load_acc<SMEM, 4 * d>(r, lim, M, p, Dp);
         if constexpr (GRAD) {
             // d log P / d iz = 1/iz - u^2 + X Cz - (Qz/2)(1/Q + X^2)
             // d log P / d il = 1/(2 il) - Bl/2 + X Cl - (Ql/2)(1/Q + X^2)
@@ -288,7 +318,7 @@ __device__ __forceinline__ void pass1_step(const RowK<SMEM>& r, const RowG& rg, 
             const float cz = fmaf(fd, rg.dcz, rg.cz0);
             const float dz_ = fmaf(-qzh, S, fmaf(X, cz, fmaf(-u, u, rg.kz)));
             const float dl_ = fmaf(-rg.qlh, S, fmaf(X, rg.cl, rg.kl));
-            if (M < r.len) {
+            if (M < lim) {
                 const float wgt = p * rhop;
                 Ez = fmaf(wgt, dz_, Ez);
                 El = fmaf(wgt, dl_, El);
@@ -307,7 +337,8 @@ __device__ __forceinline__ void pass2_step(const RowK<SMEM>& r, int maxlen, cons
         if constexpr ((M & 3) == 0) {
             if (M >= maxlen) return;
         }
-        red_add<SMEM, 4 * trav_delta<TRAV>(M)>(r, M, P[M] * invD);
+        red_add<SMEM, 4 * trav_delta<TRAV>(M)>(r, (M & 1) ? r.lim_odd : r.lim_even, M,
+                                               P[M] * invD);
         pass2_step<TRAV, LMAX, SMEM, M + 1>(r, maxlen, P, invD);
     }
 }
@@ -326,11 +357,9 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
     const int2 rws = evs.rows[e];
     RowK<SMEM> r;
     RowG rg;
-    if (rowi < rws.y)
-        make_row<TRAV, GRAD, SMEM>(g, ev, evs.geo64 + e, rws.x + rowi, f, rp_base, r, rg, bs);
-    else
-        row_idle<GRAD, SMEM>(r, rg);
-    const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)r.len);
+    make_row<TRAV, LMAX, GRAD, SMEM>(g, ev, evs.geo64 + e, rws.x + rowi, rowi < rws.y, f, rp_base,
+                                     r, rg, bs);
+    const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(r.lim_odd, r.lim_even));
     float P[LMAX];
     float Dp = 0.0f, Ez = 0.0f, El = 0.0f;
     pass1_step<TRAV, LMAX, GRAD, SMEM, 0>(r, rg, maxlen, P, Dp, Ez, El);
