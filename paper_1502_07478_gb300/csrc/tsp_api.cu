@@ -36,7 +36,7 @@ struct tsp_ctx {
     long long n = 0, cap = 0;
     float *zu = nullptr, *zd = nullptr, *dl = nullptr;
     float4 *geo_u = nullptr, *geo = nullptr;
-    double4 *geo64_u = nullptr, *geo64 = nullptr;
+    Ev64 *geo64_u = nullptr, *geo64 = nullptr;
     int2 *rows_u = nullptr, *rows = nullptr;
     int* key = nullptr;
     int4* items = nullptr;
@@ -377,8 +377,8 @@ int ensure_event_capacity(tsp_ctx* c, long long n)
     TSP_CUDA(c, cudaMalloc(&c->dl, sizeof(float) * n));
     TSP_CUDA(c, cudaMalloc(&c->geo_u, sizeof(float4) * n));
     TSP_CUDA(c, cudaMalloc(&c->geo, sizeof(float4) * n));
-    TSP_CUDA(c, cudaMalloc(&c->geo64_u, sizeof(double4) * n));
-    TSP_CUDA(c, cudaMalloc(&c->geo64, sizeof(double4) * n));
+    TSP_CUDA(c, cudaMalloc(&c->geo64_u, sizeof(Ev64) * n));
+    TSP_CUDA(c, cudaMalloc(&c->geo64, sizeof(Ev64) * n));
     TSP_CUDA(c, cudaMalloc(&c->rows_u, sizeof(int2) * n));
     TSP_CUDA(c, cudaMalloc(&c->rows, sizeof(int2) * n));
     TSP_CUDA(c, cudaMalloc(&c->key, sizeof(int) * n));

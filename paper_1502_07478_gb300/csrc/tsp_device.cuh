@@ -100,10 +100,26 @@ struct Accum {
     int pad1[3];
 };
 
+// Double-precision event geometry (y~, z~, tan theta~, 1 + tan^2), 32-byte
+// aligned so that one event is one 32-byte load.
+struct __align__(32) Ev64 {
+    double x, y, z, w;
+};
+
+__host__ __device__ __forceinline__ Ev64 make_ev64(double x, double y, double z, double w)
+{
+    Ev64 e;
+    e.x = x;
+    e.y = y;
+    e.z = z;
+    e.w = w;
+    return e;
+}
+
 // Prepared events in binned order.
 struct EventsView {
     const float4* __restrict__ geo;    // (yt, zt, t, c2i) per event, rounded from geo64
-    const double4* __restrict__ geo64; // (yt, zt, t, c2i) in double precision
+    const Ev64* __restrict__ geo64; // (yt, zt, t, c2i) in double precision
     const int2* __restrict__ rows;     // (first row, row count) of the non-empty chords
 };
 
@@ -140,14 +156,14 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads)
 // Eq. 2 (first forms) for one event, in double precision; returns false for
 // non-finite input.  ev = (y~, z~, tan theta~, 1 + tan^2).
 __device__ __forceinline__ bool direct_reconstruction(const Geo& g, float zu, float zd, float dl,
-                                                      double4& ev)
+                                                      Ev64& ev)
 {
     if (!(isfinite(zu) && isfinite(zd) && isfinite(dl))) return false;
     const double t = ((double)zu - (double)zd) / (2.0 * g.Rd);
     const double c2i = 1.0 + t * t;
     const double yt = -0.5 * (double)dl / sqrt(c2i);
     const double zt = 0.5 * ((double)zu + (double)zd + 2.0 * yt * t);
-    ev = make_double4(yt, zt, t, c2i);
+    ev = make_ev64(yt, zt, t, c2i);
     return true;
 }
 
@@ -181,7 +197,7 @@ struct Chord {
 constexpr float kEndRel = 1e-6f;
 constexpr float kRemRel = 1e-5f;
 
-__device__ __forceinline__ void chord_fp64(const Geo& g, const double4& e, int iy, int& lo,
+__device__ __forceinline__ void chord_fp64(const Geo& g, const Ev64& e, int iy, int& lo,
                                            int& count)
 {
     const double y = g.y0d + (double)iy * g.dyd;
@@ -206,7 +222,7 @@ __device__ __forceinline__ void chord_fp64(const Geo& g, const double4& e, int i
 // event preparation and the MLEM passes derive bit-identical chords whatever
 // the surrounding code lets the compiler fuse.
 __device__ __forceinline__ Chord row_chord(const Geo& g, const float4& ev,
-                                           const double4* __restrict__ ev64, int iy)
+                                           const Ev64* __restrict__ ev64, int iy)
 {
     Chord c;
     c.y = __fmaf_rn((float)iy, g.dy, g.y0);

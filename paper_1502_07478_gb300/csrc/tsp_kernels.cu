@@ -59,7 +59,7 @@ __global__ void k_sensitivity(double R, double L, int ny, int nz, double dy, dou
 // bin_count has nbins entries; the last bin collects the outliers.
 __global__ void k_setup(Geo g, Tiling tl, long long n, const float* __restrict__ zu,
                         const float* __restrict__ zd, const float* __restrict__ dl,
-                        float4* __restrict__ geo, double4* __restrict__ geo64,
+                        float4* __restrict__ geo, Ev64* __restrict__ geo64,
                         int2* __restrict__ rows, int* __restrict__ key,
                         unsigned long long* counters, int* bin_count, int nbins)
 {
@@ -72,7 +72,7 @@ __global__ void k_setup(Geo g, Tiling tl, long long n, const float* __restrict__
     unsigned long long bad = 0, empty = 0, outl = 0, pix = 0;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
          j += (long long)gridDim.x * blockDim.x) {
-        double4 e64 = make_double4(0.0, 0.0, 0.0, 1.0);
+        Ev64 e64 = make_ev64(0.0, 0.0, 0.0, 1.0);
         float4 ev = make_float4(0.f, 0.f, 0.f, 1.f);
         int k = kKeyEmpty;
         int2 rw = make_int2(0, 0);
@@ -153,9 +153,9 @@ __global__ void k_setup(Geo g, Tiling tl, long long n, const float* __restrict__
 // block the rank of an event in its bin comes from a shared-memory counter and
 // one global reservation is made per (block, bin).
 __global__ void k_scatter(long long n, int nbins, const int* __restrict__ key,
-                          const float4* __restrict__ geo_in, const double4* __restrict__ g64_in,
+                          const float4* __restrict__ geo_in, const Ev64* __restrict__ g64_in,
                           const int2* __restrict__ rows_in, const long long* __restrict__ offsets,
-                          int* cursor, float4* __restrict__ geo_out, double4* __restrict__ g64_out,
+                          int* cursor, float4* __restrict__ geo_out, Ev64* __restrict__ g64_out,
                           int2* __restrict__ rows_out)
 {
     extern __shared__ int s_cnt[];   // [nbins] local counts, then [nbins] reserved bases
@@ -182,10 +182,10 @@ __global__ void k_scatter(long long n, int nbins, const int* __restrict__ key,
 
 __global__ void k_scatter_global(long long n, const int* __restrict__ key,
                                  const float4* __restrict__ geo_in,
-                                 const double4* __restrict__ g64_in,
+                                 const Ev64* __restrict__ g64_in,
                                  const int2* __restrict__ rows_in,
                                  const long long* __restrict__ offsets, int* cursor,
-                                 float4* __restrict__ geo_out, double4* __restrict__ g64_out,
+                                 float4* __restrict__ geo_out, Ev64* __restrict__ g64_out,
                                  int2* __restrict__ rows_out)
 {
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
@@ -293,7 +293,7 @@ cudaError_t launch_sensitivity(double R, double L, int ny, int nz, double dy, do
 }
 
 cudaError_t launch_setup(const Geo& g, const Tiling& tl, long long n, const float* zu,
-                         const float* zd, const float* dl, float4* geo, double4* geo64, int2* rows,
+                         const float* zd, const float* dl, float4* geo, Ev64* geo64, int2* rows,
                          int* key, unsigned long long* counters, int* bin_count, int nbins,
                          cudaStream_t st)
 {
@@ -305,8 +305,8 @@ cudaError_t launch_setup(const Geo& g, const Tiling& tl, long long n, const floa
 }
 
 cudaError_t launch_scatter(long long n, int nbins, const int* key, const float4* geo_in,
-                           const double4* g64_in, const int2* rows_in, const long long* offsets,
-                           int* cursor, float4* geo_out, double4* g64_out, int2* rows_out,
+                           const Ev64* g64_in, const int2* rows_in, const long long* offsets,
+                           int* cursor, float4* geo_out, Ev64* g64_out, int2* rows_out,
                            cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;

@@ -41,12 +41,12 @@ cudaError_t prepare_pass_l(int mode, size_t smem);
 cudaError_t launch_sensitivity(double R, double L, int ny, int nz, double dy, double dz, float* s,
                                cudaStream_t st);
 cudaError_t launch_setup(const Geo& g, const Tiling& tl, long long n, const float* zu,
-                         const float* zd, const float* dl, float4* geo, double4* geo64, int2* rows,
+                         const float* zd, const float* dl, float4* geo, Ev64* geo64, int2* rows,
                          int* key, unsigned long long* counters, int* bin_count, int nbins,
                          cudaStream_t st);
 cudaError_t launch_scatter(long long n, int nbins, const int* key, const float4* geo_in,
-                           const double4* g64_in, const int2* rows_in, const long long* offsets,
-                           int* cursor, float4* geo_out, double4* g64_out, int2* rows_out,
+                           const Ev64* g64_in, const int2* rows_in, const long long* offsets,
+                           int* cursor, float4* geo_out, Ev64* g64_out, int2* rows_out,
                            cudaStream_t st);
 cudaError_t launch_begin(Accum* accum, cudaStream_t st);
 cudaError_t launch_finalize(int npix, float* rho, float* rhop, float* A, const float* s,

@@ -112,7 +112,7 @@ __device__ __forceinline__ void row_idle(RowK<SMEM>& r, RowG& rg)
 // the clamp keeps every access in bounds regardless (clipped pixels are
 // counted).
 template <int TRAV, int LMAX, bool GRAD, bool SMEM>
-__device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const double4* ev64,
+__device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const Ev64* ev64,
                                          int iy, bool valid_row, const Frame* fp,
                                          const float* base, RowK<SMEM>& r, RowG& rg,
                                          BlockSums* bs)
