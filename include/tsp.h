@@ -31,6 +31,7 @@
 #ifndef TSP_H
 #define TSP_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -151,6 +152,44 @@ int tsp_stats(tsp_ctx* ctx, tsp_stats_t* out, void* stream);
  * written (at most max).  Synchronises stream. */
 int tsp_set_profiling(tsp_ctx* ctx, int on);
 int tsp_pass_times(tsp_ctx* ctx, float* ms, int max, int* count, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Allocation-free MLEM update (no counterpart in the paper: an interface for
+ * callers that cannot allocate device memory -- code running under a fixed
+ * memory budget handed out by a host framework, real-time acquisition loops
+ * where an allocation and the synchronisation it may imply are not allowed,
+ * plug-ins that must not touch their host process's allocator).
+ *
+ * One list-mode MLEM update of Eq. iter, rho_out = rho_in * sum_j P_j / D_j,
+ * computed by the same kernels as tsp_iterate.  All pointers except params and
+ * errbuf are device pointers owned by the caller: zu, zd, dl (n floats each),
+ * s (ny*nz, the sensitivity map, e.g. from tsp_compute_sensitivity), rho_in
+ * and rho_out (ny*nz each; rho_out must not alias rho_in).  Non-finite events
+ * are skipped.  Enqueued on stream; returns without synchronising.
+ *
+ * The call allocates nothing: no cudaMalloc, no cudaFree, no host heap.  Its
+ * scratch (staged rho', back-projection accumulator, one chunk of prepared
+ * events, counters) is a file-scope static device array of
+ * TSP_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
+ * until the process exits.  Limits: ny*nz <= TSP_NOALLOC_MAX_PIXELS (larger
+ * images return TSP_EINVAL with a message); events are processed in chunks of
+ * TSP_NOALLOC_CHUNK, any n >= 0 is accepted.
+ *
+ * The first call on a device looks up the device address of the scratch array
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array and
+ * it keeps the last call's contents (the call clears what must start at
+ * zero): calls that overlap on the GPU (different streams or host threads)
+ * race and give wrong results, so serialise them.
+ *
+ * errbuf (nullable, errlen bytes) receives a message on failure.  Returns 0 or
+ * a TSP_E* code. */
+#define TSP_NOALLOC_MAX_PIXELS (1 << 20)
+#define TSP_NOALLOC_CHUNK (1 << 16)
+#define TSP_NOALLOC_SCRATCH_BYTES (12u << 20)
+int tsp_mlem_update_noalloc(const tsp_params* params, const float* zu, const float* zd,
+                            const float* dl, int64_t n, const float* s, const float* rho_in,
+                            float* rho_out, void* stream, char* errbuf, size_t errlen);
 
 #ifdef __cplusplus
 }

@@ -61,6 +61,8 @@ SIGNATURES = [
     ("tsp_stats", C.c_int, [_vp, C.POINTER(Stats), _vp]),
     ("tsp_set_profiling", C.c_int, [_vp, C.c_int]),
     ("tsp_pass_times", C.c_int, [_vp, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int), _vp]),
+    ("tsp_mlem_update_noalloc", C.c_int, [C.POINTER(Params), _fp, _fp, _fp, C.c_int64, _fp, _fp,
+                                          _fp, _vp, C.c_char_p, C.c_size_t]),
 ]
 
 _lib = None
