@@ -186,36 +186,32 @@ struct Chord {
     float y, Dy, B0, zc;
 };
 
-// The single-precision window decision is repeated in double precision when a
+// The single-precision window decision is checked in double precision when a
 // chord end lies within a bound on its rounding error of a pixel centre, or
 // when rem = cut2 - B0 is within its own error bound of 0, so that membership
-// agrees with a double-precision evaluation of bCb <= cut^2.  The bounds are a
-// few times the worst-case error of the single-precision expressions:
+// agrees with a double-precision evaluation of bCb <= cut^2 at every pixel.
+// The bounds are a few times the worst-case error of the single-precision
+// expressions (below 2e-4 pixel on the workloads' grids):
 //   end:  kEndRel * (|x| + (|zc| + umax + |z0|)/dz)            (coordinates)
 //       + kEndRel * cut2 / sqrt(rem) / sqrt(2 iz) / dz           (from umax)
 //   rem:  kRemRel * cut2
-constexpr float kEndRel = 1e-6f;
+// The check evaluates bCb in double precision at the pixels next to the
+// uncertain end (the error is far below one pixel, so an end moves by at most
+// one column) -- only multiplications and additions, no division or root.
+constexpr float kEndRel = 5e-7f;
 constexpr float kRemRel = 1e-5f;
 
-__device__ __forceinline__ void chord_fp64(const Geo& g, const Ev64& e, int iy, int& lo,
-                                           int& count)
+// bCb of column iz in the row with offset Dy (B0 = 4 il Dy^2 c2i), double
+// precision: the window quantity of Sec. 3 for a diagonal C^-1.
+__device__ __forceinline__ double bq_fp64(const Geo& g, const Ev64& e, double Dy, double B0, int iz)
 {
-    const double y = g.y0d + (double)iy * g.dyd;
-    const double Dy = y - e.x;
-    const double rem = g.cut2d - 4.0 * g.ild * Dy * Dy * e.w;
-    lo = 0;
-    count = 0;
-    if (rem >= 0.0) {
-        const double umax = sqrt(rem / (2.0 * g.izd));
-        const double zc = e.y + e.z * Dy;
-        double flo = ceil((zc - umax - g.z0d) / g.dzd);
-        double fhi = floor((zc + umax - g.z0d) / g.dzd);
-        flo = fmin(fmax(flo, 0.0), (double)g.nz);
-        fhi = fmax(fmin(fhi, (double)(g.nz - 1)), -1.0);
-        lo = (int)flo;
-        const int hi = (int)fhi;
-        count = hi >= lo ? hi - lo + 1 : 0;
-    }
+    const double u = (g.z0d + (double)iz * g.dzd) - (e.y + e.z * Dy);
+    return 2.0 * g.izd * u * u + B0;
+}
+
+__device__ __forceinline__ int float_to_index(float x)
+{
+    return (int)fminf(fmaxf(x, -1.0e9f), 1.0e9f);
 }
 
 // Explicitly rounded operations (never contracted into FMAs), so that the
@@ -232,7 +228,9 @@ __device__ __forceinline__ Chord row_chord(const Geo& g, const float4& ev,
     c.lo = 0;
     c.count = 0;
     const float rem = __fsub_rn(g.cut2, c.B0);
-    bool unsure = fabsf(rem) < kRemRel * g.cut2;
+    const bool unsure_rem = fabsf(rem) < kRemRel * g.cut2;
+    bool unsure_lo = false, unsure_hi = false;
+    int a = 0, b = -1;                                // candidate columns [a, b]
     if (rem >= 0.0f) {
         const float sr = __fsqrt_rn(rem);
         const float umax = __fmul_rn(sr, g.inv_sqrt_2iz);
@@ -241,10 +239,43 @@ __device__ __forceinline__ Chord row_chord(const Geo& g, const float4& ev,
         const float coord = (fabsf(c.zc) + umax + fabsf(g.z0)) * g.inv_dz;
         const float m = kEndRel * (fabsf(xhi) + coord) +
                         kEndRel * g.cut2 * g.inv_sqrt_2iz * g.inv_dz / fmaxf(sr, 1e-20f);
-        unsure = unsure || fabsf(xlo - rintf(xlo)) < m || fabsf(xhi - rintf(xhi)) < m;
-        c.count = clamp_range(ceilf(xlo), floorf(xhi), g.nz, c.lo);
+        unsure_lo = fabsf(xlo - rintf(xlo)) < m;
+        unsure_hi = fabsf(xhi - rintf(xhi)) < m;
+        a = float_to_index(ceilf(xlo));
+        b = float_to_index(floorf(xhi));
     }
-    if (unsure) chord_fp64(g, *ev64, iy, c.lo, c.count);
+    if (unsure_rem || unsure_lo || unsure_hi) {
+        const Ev64 e = *ev64;
+        const double Dy = (g.y0d + (double)iy * g.dyd) - e.x;
+        const double B0 = 4.0 * g.ild * Dy * Dy * e.w;
+        if (unsure_rem) {
+            // at most a few pixels around the chord centre can be inside
+            const int k = float_to_index(rintf(__fmul_rn(__fsub_rn(c.zc, g.z0), g.inv_dz)));
+            a = 0;
+            b = -1;
+            for (int iz = k - 2; iz <= k + 2; ++iz) {
+                if (bq_fp64(g, e, Dy, B0, iz) <= g.cut2d) {
+                    if (b < a) a = iz;
+                    b = iz;
+                }
+            }
+        } else {
+            if (unsure_lo) {
+                if (bq_fp64(g, e, Dy, B0, a - 1) <= g.cut2d) --a;
+                else if (bq_fp64(g, e, Dy, B0, a) > g.cut2d) ++a;
+            }
+            if (unsure_hi) {
+                if (bq_fp64(g, e, Dy, B0, b + 1) <= g.cut2d) ++b;
+                else if (bq_fp64(g, e, Dy, B0, b) > g.cut2d) --b;
+            }
+        }
+    }
+    if (b >= a) {
+        c.lo = max(a, 0);
+        const int hi = min(b, g.nz - 1);
+        c.count = hi >= c.lo ? hi - c.lo + 1 : 0;
+        if (c.count == 0) c.lo = 0;
+    }
     return c;
 }
 
