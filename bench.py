@@ -8,7 +8,11 @@ step is one full reconstruction: reset the image and apply the 20 MLEM
 iterations (tsp_iterate, replayed from a CUDA graph) with the events resident
 in HBM.  value = events x iterations x steps / time of the timed steps.
 
-Also reported: the same metric end to end through the C ABI with host buffers
+Also reported: batched vs plain on the batched workload (64 reconstructions
+with their own grids, resolutions and event counts, 10 iterations each; one
+tsp_batch with the autotuned schedule against 64 plain contexts run one after
+another, images compared), the same metric end to end through the C ABI with
+host buffers
 (e2e: pinned-host event upload, per-event preparation and binning, the
 iterations and the image readout, every step), the dominant kernel's achieved
 pixel-evaluation rate against the SFU (MUFU) roofline, and the FP64 CPU oracle
@@ -184,6 +188,236 @@ def run_reference(args, workload):
     return 0
 
 
+def rel_err_images(a, b, frac=0.01):
+    """max |a - b| / b over the pixels of b above frac * max(b)."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    m = b > frac * b.max()
+    return float(np.max(np.abs(a[m] - b[m]) / b[m])) if m.any() else 0.0
+
+
+def bench_batched(steps: int, warmup: int, k: int = 64, seed: int = 3):
+    """Batched vs plain on the batched workload: k reconstructions (seeded 2-6
+    ellipse phantoms, 1/2/4 mm pixels, 1e4-2e6 events, sigma_z 8-12 mm,
+    sigma_dl 30-50 mm, 10 iterations each).  Plain: one context per
+    reconstruction, iterated one after another on one stream.  Batched: one
+    tsp_batch with the autotuned schedule.  One step = reset every image and
+    apply the 10 iterations to all k.  Images of the two forms are compared."""
+    import torch
+    from paper_1502_07478_gb300 import Batch, Recon
+    from synth import batched_instances
+    ws = batched_instances(k, seed=seed)
+    evs = [w.events() for w in ws]
+    n_iter = ws[0].n_iter
+    total = sum(w.n_events for w in ws)
+    stream = torch.cuda.current_stream()
+
+    def timed(step):
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    plain = []
+    for w, ev in zip(ws, evs):
+        r = Recon.from_workload(w)
+        r.upload_events(*ev)
+        plain.append(r)
+
+    def plain_step():
+        for r in plain:
+            r.set_image(None)
+            r.iterate(n_iter)
+
+    l0 = sum(r.stats()["launches"] for r in plain)
+    t_plain = timed(plain_step)
+    l_plain = (sum(r.stats()["launches"] for r in plain) - l0) / (steps + warmup)
+    img_plain = [r.read_image().cpu().numpy() for r in plain]
+    for r in plain:
+        r.close()
+
+    b = Batch.from_workloads(ws)
+    for i, ev in enumerate(evs):
+        b.upload_events(i, *ev)
+    t0 = time.perf_counter()
+    sched, tuned_ms = b.autotune()
+    t_tune = time.perf_counter() - t0
+
+    def batch_step():
+        for i in range(k):
+            b.set_image(i, None)
+        b.iterate(n_iter)
+
+    b0 = b.stats(0)["launches"]
+    t_batch = timed(batch_step)
+    l_batch = (b.stats(0)["launches"] - b0) / (steps + warmup)
+    err = max(rel_err_images(b.read_image(i).cpu().numpy(), img_plain[i]) for i in range(k))
+    used = sum(b.stats(i)["n_used"] for i in range(k))
+    b.close()
+    return {"workload": f"batched_{k}", "instances": k, "events": total,
+            "iterations_per_step": n_iter, "steps": steps,
+            "pixel_mm": sorted({w.dz for w in ws}),
+            "batched": total * n_iter * steps / t_batch, "plain": total * n_iter * steps / t_plain,
+            "unit": UNIT, "speedup": t_plain / t_batch,
+            "ms_per_step": {"batched": 1e3 * t_batch / steps, "plain": 1e3 * t_plain / steps},
+            "kernel_launches_per_step": {"batched": l_batch, "plain": l_plain},
+            "rel_err_batched_vs_plain": err, "n_used": used,
+            "schedule": sched, "autotune": {"best_pass_ms": tuned_ms, "seconds": t_tune}}
+
+
+def _make_chunk(args):
+    name, n_events, k, chunk = args
+    from synth import make_workload
+    return make_workload(name, n_events=n_events).event_chunk(k, chunk)
+
+
+def _make_events(args):
+    w = args
+    return w.events()
+
+
+def bench_stress(args, workload, chunk: int = 10_000_000):
+    """The stress workload: 0.5 mm pixels (1400 x 1000), 1e8 events streamed to
+    the device in 1e7-event pinned chunks (tsp_begin/append/end_events), 10
+    iterations; plus the adjoint pass of 16 independent 2 mm reconstructions
+    (1e6 events each) batched in one launch against 16 plain passes.  Warm-up
+    is 3 single iterations; a timed step is the workload's 10 iterations."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    sizes = workload.chunk_sizes(chunk)
+    from synth import make_workload
+    adj = [make_workload("adjoint_2mm", seed=4 + 1000 * (i + 1)) for i in range(16)]
+    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 4),
+                                mp_context=mp.get_context("spawn")) as ex:
+        chunks = list(ex.map(_make_chunk, [(workload.name, workload.n_events, k, chunk)
+                                           for k in range(len(sizes))]))
+        adj_ev = list(ex.map(_make_events, adj))
+    import torch
+    from paper_1502_07478_gb300 import Batch, Recon
+    torch.cuda.set_device(0)
+    pinned = [[torch.from_numpy(x).pin_memory() for x in c] for c in chunks]
+    stream = torch.cuda.current_stream()
+    n = workload.n_events
+    n_iter = workload.n_iter
+    r = Recon.from_workload(workload)
+    out = torch.empty((workload.ny, workload.nz), dtype=torch.float32).pin_memory()
+
+    def upload():
+        r.begin_events(n)
+        for c in pinned:
+            r.append_events(*c)
+        r.end_events()
+
+    upload()                                  # allocation and first-use costs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    upload()
+    r.iterate(n_iter)
+    r.read_image(out=out.numpy())
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    r.set_profiling(True)
+    for _ in range(3):
+        r.iterate(1)
+    r.set_image(None)
+    torch.cuda.synchronize()
+    st0 = r.stats()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        r.set_image(None)
+        r.iterate(n_iter)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    pass_ms = r.pass_times()
+    st1 = r.stats()
+    s_map = r.compute_sensitivity().double()
+    rho = r.read_image().double()
+    cons = float((s_map * rho).sum()) / max(1, st1["n_used"]) - 1.0
+    r.close()
+    del pinned
+
+    # batched adjoint: 16 reconstructions, gradients at sigma = (14, 55)
+    b = Batch.from_workloads(adj)
+    plain = []
+    for i, (w, ev) in enumerate(zip(adj, adj_ev)):
+        b.upload_events(i, *ev)
+        b.set_sigma(i, 14.0, 55.0)
+        p = Recon.from_workload(w)
+        p.upload_events(*ev)
+        p.set_sigma(14.0, 55.0)
+        plain.append(p)
+    b.loglik_grad()
+    for p in plain:
+        p.loglik_grad(want_rho=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Lb, gsb = b.loglik_grad()
+    t_b = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    res = [p.loglik_grad() for p in plain]
+    t_p = time.perf_counter() - t0
+    gerr = max(float((b.read_image(i, 2) - res[i][1]).norm() / res[i][1].norm())
+               for i in range(len(adj)))
+    Lerr = max(abs(Lb[i] / res[i][0] - 1) for i in range(len(adj)))
+    n_adj = sum(w.n_events for w in adj)
+    b.close()
+    for p in plain:
+        p.close()
+
+    W = st1["n_window"]
+    t_pass = float(np.mean(pass_ms[-n_iter:])) / 1e3 if pass_ms else float("nan")
+    props = torch.cuda.get_device_properties(0)
+    peaks = _peaks()
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak = props.multi_processor_count * f_max * MUFU_PER_SM_CLK / MUFU_PER_PIXEL
+    cpu = None if args.no_cpu_baseline else cpu_baseline(workload, target_s=10.0)
+    line = {
+        "metric": METRIC, "value": n * n_iter * args.steps / (ms / 1e3), "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": 3, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded phantom events, streamed form: chunk k from seed (5, k))",
+        "config": {"workload": workload.name, "events": n, "iterations_per_step": n_iter,
+                   "grid": [workload.ny, workload.nz], "pixel_mm": workload.dz,
+                   "sigma_z": workload.sigma_z, "sigma_dl": workload.sigma_dl,
+                   "cut": workload.cut, "form": "plain, streamed upload",
+                   "upload": f"{len(sizes)} pinned chunks of <= {chunk} events",
+                   "warmup": "3 single iterations",
+                   "l2": "inputs larger than L2", "parallelism": "1 GPU"},
+        "roofline": {"bound": "alu", "achieved": W / t_pass / 1e9 if pass_ms else None,
+                     "peak": peak / 1e9, "unit": "Gpixel-evals/s",
+                     "frac": (W / t_pass / peak) if pass_ms else None, "traffic": None,
+                     "kernel": "MLEM pass (global-memory path), per launch",
+                     "pixel_evals_per_launch": W, "launch_ms": t_pass * 1e3},
+        "cpu_baseline": cpu,
+        "e2e": {"value": n * n_iter / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 4 * workload.ny * workload.nz,
+                "steps": 1, "includes": "streamed upload + binning + iterations + readout"},
+        "adjoint_batched_16": {"instances": 16, "events": n_adj, "grid": [350, 250],
+                               "batched_s": t_b, "plain_s": t_p, "speedup": t_p / t_b,
+                               "events_per_s_batched": n_adj / t_b,
+                               "max_rel_err_g_rho_vs_plain": gerr, "max_rel_err_L_vs_plain": Lerr},
+        "gpu_launches": st1["launches"] - st0["launches"], "clocks": clk,
+        "checks": {"conservation_rel": cons, "n_used": st1["n_used"],
+                   "n_outliers": st1["n_outliers"], "n_empty": st1["n_empty"]},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -195,6 +429,8 @@ def main():
     ap.add_argument("--iters", type=int, default=None, help="override iterations per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-vs-plain comparison")
     args = ap.parse_args()
 
     from synth import make_workload
@@ -208,6 +444,11 @@ def main():
     if args.impl == "reference":
         return run_reference(args, workload)
 
+    if workload.name == "stress_05mm":
+        if ws > 1:
+            print(json.dumps({"error": "the stress workload runs on one GPU"}))
+            return 1
+        return bench_stress(args, workload)
     import torch
     if not torch.cuda.is_available():
         print(json.dumps({"error": "no CUDA device"}))
@@ -318,6 +559,10 @@ def main():
                "h2d_bytes_per_step": int(sum(p.numel() * 4 for p in pinned)),
                "d2h_bytes_per_step": int(pinned_out.numel() * 4), "steps": k_e2e}
 
+    batched = None
+    if not args.no_batched and ws == 1:
+        batched = bench_batched(steps=max(1, min(args.steps, 2)), warmup=1)
+
     if rank != 0:
         if pg:
             pg.destroy_process_group()
@@ -337,7 +582,8 @@ def main():
                    "cut": workload.cut, "form": "plain",
                    "l2": "inputs larger than L2 (prepared events 24 B x 1e7 = 240 MB)",
                    "parallelism": f"{ws} independent reconstructions" if ws > 1 else "1 GPU"},
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
+        "gpu_launches": launches,
         "clocks": clk,
         "checks": {"conservation_rel": cons, "n_used": st1["n_used"],
                    "n_outliers": st1["n_outliers"], "n_empty": st1["n_empty"]},

@@ -101,6 +101,23 @@ const char* tsp_version(void);
 int tsp_upload_events(tsp_ctx* ctx, const float* zu, const float* zd, const float* dl,
                       int64_t n, int on_device, void* stream);
 
+/* Streamed upload: the same result as tsp_upload_events of the concatenated
+ * chunks, for event sets that are produced or staged in pieces.
+ * tsp_begin_events reserves room for n_total events and clears the binning;
+ * each tsp_append_events copies one chunk (host or device) and prepares it
+ * (Eq. 2, window, bin key) while later chunks are still arriving: host chunks
+ * are copied on a copy stream of the context, so with pinned host memory the
+ * copy of chunk k+1 overlaps the preparation of chunk k.  A host chunk must
+ * stay valid and unmodified until `stream` has been synchronised (the call
+ * returns before the copy ends).  tsp_end_events bins the appended events,
+ * resets the image to rho = 1 and synchronises.  Appending more than n_total
+ * events gives TSP_EINVAL; append / end without begin, and iterate,
+ * set_sigma or set_schedule between begin and end, give TSP_ESTATE. */
+int tsp_begin_events(tsp_ctx* ctx, int64_t n_total, void* stream);
+int tsp_append_events(tsp_ctx* ctx, const float* zu, const float* zd, const float* dl,
+                      int64_t n, int on_device, void* stream);
+int tsp_end_events(tsp_ctx* ctx, void* stream);
+
 /* Sensitivity map s(y, z) of Eq. s-yz at the pixel centres (clamped at 0).
  * out (nullable) receives ny*nz floats, host or device (on_device). */
 int tsp_compute_sensitivity(tsp_ctx* ctx, float* out, int on_device, void* stream);
@@ -152,6 +169,91 @@ int tsp_stats(tsp_ctx* ctx, tsp_stats_t* out, void* stream);
  * written (at most max).  Synchronises stream. */
 int tsp_set_profiling(tsp_ctx* ctx, int on);
 int tsp_pass_times(tsp_ctx* ctx, float* ms, int max, int* count, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Tile schedule (no counterpart in the paper, whose kernel takes one event
+ * per warp and reads rho through the texture cache, Sec. 4).  Events are
+ * binned by the image tile of their window centre; a work item is a run of
+ * the events of one tile, staged with its halo in shared memory.  The knobs:
+ *   ty_cap        largest tile height in image rows, 4..128 (the shared-
+ *                 memory budget may force a smaller one)
+ *   items_per_sm  target work items per SM, 1..64: a tile's events are cut
+ *                 into items of placed / (items_per_sm * SMs) events,
+ *                 clamped to [32, 4096]
+ *   order         batches only: 0 = longest estimated item first,
+ *                 1 = round robin over the reconstructions
+ *   reserved      0
+ * Results do not depend on the schedule beyond float rounding order. */
+typedef struct {
+    int32_t ty_cap;
+    int32_t items_per_sm;
+    int32_t order;
+    int32_t reserved;
+} tsp_schedule;
+
+/* Current schedule of ctx (default 128, 8, 0). */
+int tsp_get_schedule(tsp_ctx* ctx, tsp_schedule* out);
+/* Set the schedule; the uploaded events are re-binned (images are kept).
+ * Invalid knobs give TSP_EINVAL and change nothing. */
+int tsp_set_schedule(tsp_ctx* ctx, const tsp_schedule* sched, void* stream);
+/* Autotuner: time one MLEM pass (best of 2, CUDA events on stream) for
+ * candidate schedules by coordinate descent over items_per_sm in
+ * {2,4,8,16,32} then ty_cap in {16,32,64,128}, keep the fastest and return it
+ * in *chosen and its pass time (ms) in *best_ms (both nullable).  The image
+ * is left unchanged.  Requires an upload (TSP_ESTATE).  Synchronises. */
+int tsp_autotune(tsp_ctx* ctx, tsp_schedule* chosen, float* best_ms, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batches: k independent reconstructions (each with its own geometry, grid,
+ * resolution, events and image) advanced together.  Each MLEM iteration of a
+ * batch is three kernel launches whatever k: a reset of the pass
+ * accumulators, one persistent tile pass over the work items of every
+ * reconstruction (plus one launch for outlier events when some
+ * reconstruction has them), and the image update of all reconstructions;
+ * n iterations are replayed from one CUDA graph.  Results equal those of k
+ * separate contexts up to float rounding order.  A batch is not thread-safe.
+ * Indices i are 0..k-1; an index out of range gives TSP_EINVAL. */
+typedef struct tsp_batch tsp_batch;
+
+/* Create a batch from k >= 1 parameter sets (params[0..k-1]), each validated
+ * as by tsp_create.  *out is NULL on failure. */
+int tsp_batch_create(const tsp_params* params, int k, tsp_batch** out);
+/* Free the batch and every reconstruction in it (NULL is accepted). */
+void tsp_batch_destroy(tsp_batch* batch);
+/* Message of the last failure on batch (or of the last failed
+ * tsp_batch_create when batch is NULL). */
+const char* tsp_batch_last_error(const tsp_batch* batch);
+/* Number of reconstructions k (0 for NULL). */
+int tsp_batch_size(const tsp_batch* batch);
+/* As tsp_upload_events / tsp_set_image / tsp_set_sigma, for reconstruction i. */
+int tsp_batch_upload_events(tsp_batch* batch, int i, const float* zu, const float* zd,
+                            const float* dl, int64_t n, int on_device, void* stream);
+int tsp_batch_set_image(tsp_batch* batch, int i, const float* rho, int on_device, void* stream);
+int tsp_batch_set_sigma(tsp_batch* batch, int i, double sigma_z, double sigma_dl, void* stream);
+/* Apply n_iter >= 0 MLEM updates (Eq. iter) to every reconstruction.  Every
+ * reconstruction needs an upload (TSP_ESTATE otherwise).  Asynchronous. */
+int tsp_batch_iterate(tsp_batch* batch, int n_iter, void* stream);
+/* Copy an image of reconstruction i to out (its ny*nz floats, host or
+ * device): which = 0 rho, 1 rho' = s rho, 2 the g_rho of the last
+ * tsp_batch_loglik_grad. */
+int tsp_batch_read_image(tsp_batch* batch, int i, float* out, int which, int on_device,
+                         void* stream);
+/* Log-likelihood and gradients (as tsp_loglik_grad) of every reconstruction
+ * in one batched pass: L_out[i] (k doubles) and g_sigma[2i], g_sigma[2i+1]
+ * (2k doubles), each nullable; g_rho is kept on the device for
+ * tsp_batch_read_image(which = 2).  Synchronises. */
+int tsp_batch_loglik_grad(tsp_batch* batch, double* L_out, double* g_sigma, void* stream);
+/* Counters of reconstruction i (launches counts the batch's launches). */
+int tsp_batch_stats(tsp_batch* batch, int i, tsp_stats_t* out, void* stream);
+/* Schedule of the batch (shared by its reconstructions) and its autotuner:
+ * as tsp_autotune, with item order in {0, 1} tried first, timing one batched
+ * MLEM pass per candidate. */
+int tsp_batch_get_schedule(tsp_batch* batch, tsp_schedule* out);
+int tsp_batch_set_schedule(tsp_batch* batch, const tsp_schedule* sched, void* stream);
+int tsp_batch_autotune(tsp_batch* batch, tsp_schedule* chosen, float* best_ms, void* stream);
+/* As tsp_set_profiling / tsp_pass_times, for the batched pass. */
+int tsp_batch_set_profiling(tsp_batch* batch, int on);
+int tsp_batch_pass_times(tsp_batch* batch, float* ms, int max, int* count, void* stream);
 
 /* ------------------------------------------------------------------------
  * Allocation-free MLEM update (no counterpart in the paper: an interface for

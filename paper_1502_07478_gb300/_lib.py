@@ -41,6 +41,11 @@ class Stats(C.Structure):
                 ("sum_s_rho", C.c_double)]
 
 
+class Schedule(C.Structure):
+    _fields_ = [("ty_cap", C.c_int32), ("items_per_sm", C.c_int32), ("order", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 # (name, restype, argtypes) of every exported entry point
 _vp = C.c_void_p
 _fp = C.c_void_p          # float* (host or device address)
@@ -50,6 +55,9 @@ SIGNATURES = [
     ("tsp_last_error", C.c_char_p, [_vp]),
     ("tsp_version", C.c_char_p, []),
     ("tsp_upload_events", C.c_int, [_vp, _fp, _fp, _fp, C.c_int64, C.c_int, _vp]),
+    ("tsp_begin_events", C.c_int, [_vp, C.c_int64, _vp]),
+    ("tsp_append_events", C.c_int, [_vp, _fp, _fp, _fp, C.c_int64, C.c_int, _vp]),
+    ("tsp_end_events", C.c_int, [_vp, _vp]),
     ("tsp_compute_sensitivity", C.c_int, [_vp, _fp, C.c_int, _vp]),
     ("tsp_set_image", C.c_int, [_vp, _fp, C.c_int, _vp]),
     ("tsp_iterate", C.c_int, [_vp, C.c_int, _vp]),
@@ -61,6 +69,26 @@ SIGNATURES = [
     ("tsp_stats", C.c_int, [_vp, C.POINTER(Stats), _vp]),
     ("tsp_set_profiling", C.c_int, [_vp, C.c_int]),
     ("tsp_pass_times", C.c_int, [_vp, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int), _vp]),
+    ("tsp_get_schedule", C.c_int, [_vp, C.POINTER(Schedule)]),
+    ("tsp_set_schedule", C.c_int, [_vp, C.POINTER(Schedule), _vp]),
+    ("tsp_autotune", C.c_int, [_vp, C.POINTER(Schedule), C.POINTER(C.c_float), _vp]),
+    ("tsp_batch_create", C.c_int, [C.POINTER(Params), C.c_int, C.POINTER(_vp)]),
+    ("tsp_batch_destroy", None, [_vp]),
+    ("tsp_batch_last_error", C.c_char_p, [_vp]),
+    ("tsp_batch_size", C.c_int, [_vp]),
+    ("tsp_batch_upload_events", C.c_int, [_vp, C.c_int, _fp, _fp, _fp, C.c_int64, C.c_int, _vp]),
+    ("tsp_batch_set_image", C.c_int, [_vp, C.c_int, _fp, C.c_int, _vp]),
+    ("tsp_batch_set_sigma", C.c_int, [_vp, C.c_int, C.c_double, C.c_double, _vp]),
+    ("tsp_batch_iterate", C.c_int, [_vp, C.c_int, _vp]),
+    ("tsp_batch_read_image", C.c_int, [_vp, C.c_int, _fp, C.c_int, C.c_int, _vp]),
+    ("tsp_batch_loglik_grad", C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]),
+    ("tsp_batch_stats", C.c_int, [_vp, C.c_int, C.POINTER(Stats), _vp]),
+    ("tsp_batch_get_schedule", C.c_int, [_vp, C.POINTER(Schedule)]),
+    ("tsp_batch_set_schedule", C.c_int, [_vp, C.POINTER(Schedule), _vp]),
+    ("tsp_batch_autotune", C.c_int, [_vp, C.POINTER(Schedule), C.POINTER(C.c_float), _vp]),
+    ("tsp_batch_set_profiling", C.c_int, [_vp, C.c_int]),
+    ("tsp_batch_pass_times", C.c_int, [_vp, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int),
+                                       _vp]),
     ("tsp_mlem_update_noalloc", C.c_int, [C.POINTER(Params), _fp, _fp, _fp, C.c_int64, _fp, _fp,
                                           _fp, _vp, C.c_char_p, C.c_size_t]),
 ]
@@ -88,4 +116,10 @@ def lib():
 def check(ctx, rc: int):
     if rc != TSP_OK:
         msg = lib().tsp_last_error(ctx)
+        raise TspError(rc, msg.decode() if msg else "")
+
+
+def check_batch(batch, rc: int):
+    if rc != TSP_OK:
+        msg = lib().tsp_batch_last_error(batch)
         raise TspError(rc, msg.decode() if msg else "")

@@ -13,93 +13,19 @@
 #include <string>
 #include <vector>
 
-#include "tsp.h"
-#include "tsp_launch.h"
+#include "tsp_ctx.h"
 
 using namespace tsp;
 
-struct tsp_ctx {
-    tsp_params p{};
-    Geo g{};
-    Tiling tl{};
-    int lmax = 0, nseg = 1, G = 1;
-    int dev = 0, num_sms = 0;
-    size_t smem = 0;
-    int npix = 0;
-    int nbins = 0;
-    float* rho = nullptr;
-    float* rhop = nullptr;   // s * rho, padded by kPadFloats zeros
-    float* A = nullptr;
-    float* s = nullptr;
-    float* gbuf = nullptr;
-    Accum* accum = nullptr;
-    long long n = 0, cap = 0;
-    float *zu = nullptr, *zd = nullptr, *dl = nullptr;
-    float4 *geo_u = nullptr, *geo = nullptr;
-    Ev64 *geo64_u = nullptr, *geo64 = nullptr;
-    int2 *rows_u = nullptr, *rows = nullptr;
-    int* key = nullptr;
-    int4* items = nullptr;
-    int n_items = 0, items_cap = 0;
-    long long outlier_first = 0, n_outliers = 0;
-    unsigned long long counters_h[4] = {0, 0, 0, 0};
-    unsigned long long* counters = nullptr;
-    int* bin_count = nullptr;
-    long long* offsets = nullptr;
-    int* cursor = nullptr;
-    int* flag = nullptr;
-    bool uploaded = false, sens_ready = false;
-    long long iterations = 0;
-    cudaStream_t cap_stream = nullptr;
-    struct Graph {
-        cudaGraphExec_t exec = nullptr;
-        long long launches = 0;               // kernel nodes per replay
-        std::vector<cudaEvent_t> ev;          // start/stop pairs around each MLEM pass
-    };
-    std::map<int, Graph> graphs;
-    int last_graph = -1;                      // n_iter of the last replayed graph
-    bool profiling = false;
-    long long launches = 0;
-    std::string err;
-};
-
-namespace {
+namespace tsp_host {
 
 thread_local std::string g_create_error;
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-        else prev = -1;
-    }
-    ~DeviceGuard()
-    {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
 
 int fail(tsp_ctx* c, int code, const std::string& msg)
 {
     if (c) c->err = msg;
     else g_create_error = msg;
     return code;
-}
-
-#define TSP_CUDA(ctx, call)                                                                   \
-    do {                                                                                      \
-        cudaError_t e_ = (call);                                                              \
-        if (e_ != cudaSuccess)                                                                \
-            return fail((ctx), e_ == cudaErrorMemoryAllocation ? TSP_ENOMEM : TSP_ECUDA,      \
-                        std::string(#call) + ": " + cudaGetErrorString(e_));                  \
-    } while (0)
-
-template <class T>
-void dfree(T*& p)
-{
-    if (p) cudaFree(p);
-    p = nullptr;
 }
 
 void clear_graphs(tsp_ctx* c)
@@ -116,6 +42,16 @@ void clear_graphs(tsp_ctx* c)
 long long pass_launches(const tsp_ctx* c)
 {
     return (c->n_items > 0 ? 1 : 0) + (c->n_outliers > 0 ? 1 : 0);
+}
+
+size_t dyn_smem_limit(int dev)
+{
+    int optin = 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess ||
+        optin <= 0)
+        optin = 227 * 1024;
+    return (size_t)optin - 2048;    // room for the kernels' static shared memory
 }
 
 // Derive the kernel constants, lane capacity, group size and tiling from the
@@ -178,9 +114,11 @@ int plan(tsp_ctx* c)
     if (!best_l) return fail(c, TSP_EINVAL, "window chords too long for the compiled lane capacities");
     c->lmax = best_l;
     c->nseg = best_s;
+    c->need = need;
     // rows of a window: |Dy| <= cut sigma_dl cos / 2
     const double hy = cut * p.sigma_dl / 2.0 * 1.00001;
     const int maxrows = (int)std::floor(2.0 * hy / dy) + 2;
+    c->maxrows = maxrows;
     c->G = c->nseg * ((maxrows + 31) / 32);
     if (c->G > kWarps) return fail(c, TSP_EINVAL, "window has more rows than one block can hold");
 
@@ -210,18 +148,27 @@ int plan(tsp_ctx* c)
     tl.RW = RS;
     tl.TZ = RS - 2 * tl.HZ;
     const size_t budget = 200 * 1024;
-    int TY = 128;
+    int TY = std::max(4, std::min(128, c->sched.ty_cap) / 4 * 4);
     while (TY > 4 && tiles_smem_floats(TY + 2 * tl.HY, RS) * sizeof(float) > budget) TY -= 4;
-    if (tiles_smem_floats(TY + 2 * tl.HY, RS) * sizeof(float) > budget)
-        return fail(c, TSP_EINVAL, "window halo too large for shared memory");
+    if (tiles_smem_floats(TY + 2 * tl.HY, RS) * sizeof(float) > budget) {
+        // windows too large for a staged tile (very fine grids): no angle bins,
+        // so every event takes the global-memory path
+        tl.nb = 0;
+        TY = 4;
+    }
     tl.TY = std::min(TY, std::max(p.ny, 4));
     tl.RH = tl.TY + 2 * tl.HY;
     tl.tiles_y = (p.ny + tl.TY - 1) / tl.TY;
     tl.tiles_z = (p.nz + 2 * tl.zs_off + tl.TZ - 1) / tl.TZ;
-    c->smem = tiles_smem_floats(tl.RH, tl.RS) * sizeof(float);
+    c->smem = tl.nb > 0 ? tiles_smem_floats(tl.RH, tl.RS) * sizeof(float) : 0;
     c->nbins = tl.nb * tl.tiles_y * tl.tiles_z + 1;
+    // The dynamic shared-memory limit is a property of the kernel function,
+    // shared by every context: raise it to the device's opt-in maximum (never
+    // to this context's size, which could lower it below another context's).
+    const size_t limit = dyn_smem_limit(c->dev);
+    if (c->smem > limit) return fail(c, TSP_EINVAL, "tile region exceeds the shared memory");
     for (int mode = 0; mode < 3; ++mode) {
-        cudaError_t e = prepare_pass(c->lmax, mode, c->smem);
+        cudaError_t e = prepare_pass(c->lmax, mode, limit);
         if (e != cudaSuccess)
             return fail(c, TSP_ECUDA, std::string("prepare_pass: ") + cudaGetErrorString(e));
     }
@@ -286,9 +233,12 @@ PassArgs pass_args(tsp_ctx* c)
 }
 
 // Prepare the uploaded raw events: Eq. 2, windows, binning, work items.
-int prepare_events(tsp_ctx* c, cudaStream_t st)
+// Event preparation in three steps, so that an upload can be streamed in
+// chunks: clear the bin histogram and counters; per chunk, Eq. 2, windows and
+// bin keys (k_setup) for events [first, first + n); then the bin offsets, the
+// work items and the counting-sort scatter into binned order.
+int prep_begin(tsp_ctx* c, cudaStream_t st)
 {
-    const long long n = c->n;
     const int nbins = c->nbins;
     dfree(c->bin_count);
     dfree(c->offsets);
@@ -299,9 +249,23 @@ int prepare_events(tsp_ctx* c, cudaStream_t st)
     TSP_CUDA(c, cudaMemsetAsync(c->bin_count, 0, sizeof(int) * nbins, st));
     TSP_CUDA(c, cudaMemsetAsync(c->cursor, 0, sizeof(int) * nbins, st));
     TSP_CUDA(c, cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * 4, st));
-    TSP_CUDA(c, launch_setup(c->g, c->tl, n, c->zu, c->zd, c->dl, c->geo_u, c->geo64_u, c->rows_u,
-                             c->key, c->counters, c->bin_count, nbins, st));
-    c->launches += n > 0 ? 1 : 0;
+    return TSP_OK;
+}
+
+int prep_chunk(tsp_ctx* c, long long first, long long n, cudaStream_t st)
+{
+    if (n <= 0) return TSP_OK;
+    TSP_CUDA(c, launch_setup(c->g, c->tl, n, c->zu + first, c->zd + first, c->dl + first,
+                             c->geo_u + first, c->geo64_u + first, c->rows_u + first,
+                             c->key + first, c->counters, c->bin_count, c->nbins, st));
+    c->launches += 1;
+    return TSP_OK;
+}
+
+int prep_finish(tsp_ctx* c, cudaStream_t st)
+{
+    const long long n = c->n;
+    const int nbins = c->nbins;
     std::vector<int> cnt(nbins);
     TSP_CUDA(c, cudaMemcpyAsync(c->counters_h, c->counters, sizeof(c->counters_h),
                                 cudaMemcpyDeviceToHost, st));
@@ -321,24 +285,12 @@ int prepare_events(tsp_ctx* c, cudaStream_t st)
     }
     c->outlier_first = off[nbins - 1];
     c->n_outliers = cnt[nbins - 1];
-    // work items: runs of at most E events of one tile, tiles interleaved
-    long long placed = acc - c->n_outliers;
-    long long E = placed / (8ll * std::max(1, c->num_sms));
-    E = std::max(32ll, std::min(4096ll, E));
-    std::vector<int4> items;
-    for (long long k = 0;; ++k) {
-        bool any = false;
-        for (int b = 0; b < nbins - 1; ++b) {
-            const long long first = k * E;
-            if (first < cnt[b]) {
-                any = true;
-                items.push_back(make_int4(b, (int)(off[b] + first),
-                                          (int)std::min<long long>(E, cnt[b] - first), 0));
-            }
-        }
-        if (!any) break;
-    }
     if (acc > (1ll << 31) - 1) return fail(c, TSP_EINVAL, "more than 2^31-1 events");
+    c->bin_cnt = std::move(cnt);
+    c->bin_off = std::move(off);
+    const long long placed = acc - c->n_outliers;
+    const std::vector<int4> items =
+        tile_items(c, item_events(placed, c->sched.items_per_sm, c->num_sms), 0);
     c->n_items = (int)items.size();
     if (c->n_items > c->items_cap) {
         dfree(c->items);
@@ -348,7 +300,7 @@ int prepare_events(tsp_ctx* c, cudaStream_t st)
     if (c->n_items)
         TSP_CUDA(c, cudaMemcpyAsync(c->items, items.data(), sizeof(int4) * c->n_items,
                                     cudaMemcpyHostToDevice, st));
-    TSP_CUDA(c, cudaMemcpyAsync(c->offsets, off.data(), sizeof(long long) * nbins,
+    TSP_CUDA(c, cudaMemcpyAsync(c->offsets, c->bin_off.data(), sizeof(long long) * nbins,
                                 cudaMemcpyHostToDevice, st));
     TSP_CUDA(c, launch_scatter(n, nbins, c->key, c->geo_u, c->geo64_u, c->rows_u, c->offsets,
                                c->cursor, c->geo, c->geo64, c->rows, st));
@@ -356,6 +308,39 @@ int prepare_events(tsp_ctx* c, cudaStream_t st)
     clear_graphs(c);
     c->uploaded = true;
     return TSP_OK;
+}
+
+int prepare_events(tsp_ctx* c, cudaStream_t st)
+{
+    int rc = prep_begin(c, st);
+    if (!rc) rc = prep_chunk(c, 0, c->n, st);
+    if (!rc) rc = prep_finish(c, st);
+    return rc;
+}
+
+long long item_events(long long placed, int items_per_sm, int sms)
+{
+    const long long E = placed / ((long long)std::max(1, items_per_sm) * std::max(1, sms));
+    return std::max(32ll, std::min(4096ll, E));
+}
+
+std::vector<int4> tile_items(const tsp_ctx* c, long long E, int w)
+{
+    std::vector<int4> items;
+    const int nb = (int)c->bin_cnt.size() - 1;     // the last bin holds the outliers
+    for (long long k = 0;; ++k) {
+        bool any = false;
+        const long long first = k * E;
+        for (int b = 0; b < nb; ++b) {
+            if (first < c->bin_cnt[b]) {
+                any = true;
+                items.push_back(make_int4(b, (int)(c->bin_off[b] + first),
+                                          (int)std::min<long long>(E, c->bin_cnt[b] - first), w));
+            }
+        }
+        if (!any) break;
+    }
+    return items;
 }
 
 int ensure_event_capacity(tsp_ctx* c, long long n)
@@ -436,7 +421,9 @@ int copy_floats(tsp_ctx* c, float* dst, const float* src, size_t n, int dst_dev,
     return TSP_OK;
 }
 
-}  // namespace
+}  // namespace tsp_host
+
+using namespace tsp_host;
 
 extern "C" {
 
@@ -479,6 +466,8 @@ int tsp_create(const tsp_params* params, tsp_ctx** out)
     if (e == cudaSuccess) e = cudaMalloc(&c->counters, sizeof(unsigned long long) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&c->flag, sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->copy_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(c->rhop, 0, padded);
     if (e == cudaSuccess) e = cudaMemset(c->A, 0, padded);
     if (e == cudaSuccess) e = cudaMemset(c->accum, 0, sizeof(Accum));
@@ -499,6 +488,8 @@ void tsp_destroy(tsp_ctx* c)
     cudaDeviceSynchronize();
     clear_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->copy_ev) cudaEventDestroy(c->copy_ev);
     dfree(c->rho); dfree(c->rhop); dfree(c->A); dfree(c->s); dfree(c->gbuf);
     dfree(c->accum); dfree(c->counters); dfree(c->flag);
     dfree(c->zu); dfree(c->zd); dfree(c->dl);
@@ -508,28 +499,84 @@ void tsp_destroy(tsp_ctx* c)
     delete c;
 }
 
+int tsp_begin_events(tsp_ctx* c, int64_t n_total, void* stream)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (n_total < 0) return fail(c, TSP_EINVAL, "n_total < 0");
+    if (n_total > (1ll << 31) - 1) return fail(c, TSP_EINVAL, "more than 2^31-1 events");
+    DeviceGuard dg(c->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    c->uploaded = false;
+    c->appending = false;
+    clear_graphs(c);
+    // work already queued on the stream (a previous preparation reading the
+    // raw event buffers) finishes before the copy stream overwrites them
+    TSP_CUDA(c, cudaEventRecord(c->copy_ev, st));
+    TSP_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->copy_ev, 0));
+    if ((rc = ensure_event_capacity(c, std::max<long long>(n_total, 1)))) return rc;
+    if ((rc = prep_begin(c, st))) return rc;
+    c->n = 0;
+    c->n_total = n_total;
+    c->appending = true;
+    return TSP_OK;
+}
+
+int tsp_append_events(tsp_ctx* c, const float* zu, const float* zd, const float* dl, int64_t n,
+                      int on_device, void* stream)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (!c->appending) return fail(c, TSP_ESTATE, "append_events without begin_events");
+    if (n < 0) return fail(c, TSP_EINVAL, "n < 0");
+    if (n > 0 && (!zu || !zd || !dl)) return fail(c, TSP_EINVAL, "event pointer is NULL");
+    if (n > c->n_total - c->n) return fail(c, TSP_EINVAL, "more events than begin_events declared");
+    if (n == 0) return TSP_OK;
+    DeviceGuard dg(c->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    const long long first = c->n;
+    // host chunks are copied on the context's copy stream, so that the copy of
+    // the next chunk overlaps the preparation of this one
+    cudaStream_t cs = on_device ? st : c->copy_stream;
+    int rc;
+    if ((rc = copy_floats(c, c->zu + first, zu, n, 1, on_device, cs))) return rc;
+    if ((rc = copy_floats(c, c->zd + first, zd, n, 1, on_device, cs))) return rc;
+    if ((rc = copy_floats(c, c->dl + first, dl, n, 1, on_device, cs))) return rc;
+    if (!on_device) {
+        TSP_CUDA(c, cudaEventRecord(c->copy_ev, cs));
+        TSP_CUDA(c, cudaStreamWaitEvent(st, c->copy_ev, 0));
+    }
+    if ((rc = prep_chunk(c, first, n, st))) return rc;
+    c->n = first + n;
+    return TSP_OK;
+}
+
+int tsp_end_events(tsp_ctx* c, void* stream)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (!c->appending) return fail(c, TSP_ESTATE, "end_events without begin_events");
+    DeviceGuard dg(c->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    c->appending = false;
+    int rc;
+    if ((rc = ensure_sensitivity(c, st))) return rc;
+    if ((rc = prep_finish(c, st))) return rc;
+    TSP_CUDA(c, launch_fill(c->rho, c->npix, 1.0f, st));
+    c->launches += 1;
+    if ((rc = refresh_rhop(c, st))) return rc;
+    c->iterations = 0;
+    return TSP_OK;
+}
+
 int tsp_upload_events(tsp_ctx* c, const float* zu, const float* zd, const float* dl, int64_t n,
                       int on_device, void* stream)
 {
     if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
     if (n < 0) return fail(c, TSP_EINVAL, "n < 0");
     if (n > 0 && (!zu || !zd || !dl)) return fail(c, TSP_EINVAL, "event pointer is NULL");
-    if (n > (1ll << 31) - 1) return fail(c, TSP_EINVAL, "more than 2^31-1 events");
-    DeviceGuard dg(c->dev);
-    cudaStream_t st = (cudaStream_t)stream;
-    int rc;
-    if ((rc = ensure_event_capacity(c, std::max<long long>(n, 1)))) return rc;
-    c->n = n;
-    if ((rc = copy_floats(c, c->zu, zu, n, 1, on_device, st))) return rc;
-    if ((rc = copy_floats(c, c->zd, zd, n, 1, on_device, st))) return rc;
-    if ((rc = copy_floats(c, c->dl, dl, n, 1, on_device, st))) return rc;
-    if ((rc = ensure_sensitivity(c, st))) return rc;
-    if ((rc = prepare_events(c, st))) return rc;
-    TSP_CUDA(c, launch_fill(c->rho, c->npix, 1.0f, st));
-    c->launches += 1;
-    if ((rc = refresh_rhop(c, st))) return rc;
-    c->iterations = 0;
-    return TSP_OK;
+    int rc = tsp_begin_events(c, n, stream);
+    if (!rc) rc = tsp_append_events(c, zu, zd, dl, n, on_device, stream);
+    if (!rc) rc = tsp_end_events(c, stream);
+    return rc;
 }
 
 int tsp_compute_sensitivity(tsp_ctx* c, float* out, int on_device, void* stream)
@@ -654,6 +701,7 @@ int tsp_set_sigma(tsp_ctx* c, double sigma_z, double sigma_dl, void* stream)
     if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
     if (!(std::isfinite(sigma_z) && sigma_z > 0 && std::isfinite(sigma_dl) && sigma_dl > 0))
         return fail(c, TSP_EINVAL, "sigmas must be finite and > 0");
+    if (c->appending) return fail(c, TSP_ESTATE, "set_sigma between begin_events and end_events");
     DeviceGuard dg(c->dev);
     cudaStream_t st = (cudaStream_t)stream;
     tsp_params old = c->p;
@@ -705,6 +753,110 @@ int tsp_set_profiling(tsp_ctx* c, int on)
         clear_graphs(c);
         c->profiling = on != 0;
     }
+    return TSP_OK;
+}
+
+int tsp_get_schedule(tsp_ctx* c, tsp_schedule* out)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (!out) return fail(c, TSP_EINVAL, "out is NULL");
+    out->ty_cap = c->sched.ty_cap;
+    out->items_per_sm = c->sched.items_per_sm;
+    out->order = c->sched.order;
+    out->reserved = 0;
+    return TSP_OK;
+}
+
+int tsp_set_schedule(tsp_ctx* c, const tsp_schedule* s, void* stream)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (!s) return fail(c, TSP_EINVAL, "schedule is NULL");
+    if (s->ty_cap < 4 || s->ty_cap > 128 || s->items_per_sm < 1 || s->items_per_sm > 64 ||
+        (s->order != 0 && s->order != 1) || s->reserved != 0)
+        return fail(c, TSP_EINVAL,
+                    "schedule: ty_cap in [4,128], items_per_sm in [1,64], order 0 or 1, "
+                    "reserved 0");
+    if (c->appending)
+        return fail(c, TSP_ESTATE, "set_schedule between begin_events and end_events");
+    DeviceGuard dg(c->dev);
+    const Schedule old = c->sched;
+    c->sched.ty_cap = s->ty_cap;
+    c->sched.items_per_sm = s->items_per_sm;
+    c->sched.order = s->order;
+    int rc = plan(c);
+    if (rc) {
+        c->sched = old;
+        plan(c);
+        return rc;
+    }
+    clear_graphs(c);
+    if (c->uploaded && (rc = prepare_events(c, (cudaStream_t)stream))) return rc;
+    return TSP_OK;
+}
+
+int tsp_autotune(tsp_ctx* c, tsp_schedule* chosen, float* best_ms, void* stream)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (!c->uploaded) return fail(c, TSP_ESTATE, "autotune before upload_events");
+    DeviceGuard dg(c->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    TSP_CUDA(c, cudaEventCreate(&e0));
+    TSP_CUDA(c, cudaEventCreate(&e1));
+    // best of two MLEM passes; A is cleared afterwards, rho is not touched
+    auto time_pass = [&](float* ms) -> int {
+        const PassArgs a = pass_args(c);
+        float best = 1e30f;
+        for (int r = 0; r < 2; ++r) {
+            TSP_CUDA(c, launch_begin(c->accum, st));
+            TSP_CUDA(c, cudaEventRecord(e0, st));
+            TSP_CUDA(c, launch_pass(c->lmax, kMlem, a, st));
+            TSP_CUDA(c, cudaEventRecord(e1, st));
+            TSP_CUDA(c, launch_fill(c->A, c->npix, 0.0f, st));
+            TSP_CUDA(c, cudaEventSynchronize(e1));
+            float t = 0.0f;
+            TSP_CUDA(c, cudaEventElapsedTime(&t, e0, e1));
+            best = std::min(best, t);
+            c->launches += 3 + pass_launches(c);
+        }
+        *ms = best;
+        return TSP_OK;
+    };
+    tsp_schedule best{c->sched.ty_cap, c->sched.items_per_sm, c->sched.order, 0};
+    float best_t = 0.0f;
+    int rc = time_pass(&best_t);
+    auto trial = [&](tsp_schedule s) -> int {
+        int r = tsp_set_schedule(c, &s, stream);
+        float t = 0.0f;
+        if (!r) r = time_pass(&t);
+        if (r) return r;
+        if (t < best_t) {
+            best_t = t;
+            best = s;
+        }
+        return TSP_OK;
+    };
+    for (int ips : {2, 4, 8, 16, 32}) {
+        tsp_schedule s = best;
+        s.items_per_sm = ips;
+        if (!rc && ips != best.items_per_sm) rc = trial(s);
+    }
+    for (int ty : {16, 32, 64, 128}) {
+        tsp_schedule s = best;
+        s.ty_cap = ty;
+        if (!rc && ty != best.ty_cap) rc = trial(s);
+    }
+    if (!rc) rc = tsp_set_schedule(c, &best, stream);
+    if (!rc) rc = refresh_rhop(c, st);
+    if (!rc) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = fail(c, TSP_ECUDA, cudaGetErrorString(e));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (chosen) *chosen = best;
+    if (best_ms) *best_ms = best_t;
     return TSP_OK;
 }
 

@@ -123,6 +123,23 @@ struct EventsView {
     const int2* __restrict__ rows;     // (first row, row count) of the non-empty chords
 };
 
+// One reconstruction as the tile kernel reads it: its constants, tiling,
+// prepared events, rho' and back-projection buffers, pass accumulators and
+// group size (warps per event).  The plain kernel takes it as a launch
+// parameter; the batched kernel reads the record of each work item's
+// reconstruction from a device table into shared memory.
+struct Inst {
+    Geo g;
+    Tiling tl;
+    EventsView evs;
+    const float* rhop;
+    float* A;
+    Accum* accum;
+    int G;
+    int pad;
+};
+static_assert(sizeof(Inst) % 8 == 0, "Inst is copied in 8-byte words");
+
 // Key of an event in the binning: its tile index, the outlier bin (the last
 // bin), or kKeyEmpty for events whose window holds no pixel centre.
 constexpr int kKeyEmpty = -1;

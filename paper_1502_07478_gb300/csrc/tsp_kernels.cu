@@ -258,6 +258,54 @@ __global__ void k_set_rhop(int npix, const float* __restrict__ rho, const float*
     if (threadIdx.x == 0) atomicAdd(&a->sum_rhop, acc);
 }
 
+// Batched forms of k_begin and of the per-pixel kernels: blockIdx.y selects
+// the reconstruction.  op 0 = end of an MLEM iteration (k_finalize), 1 = rho'
+// refresh (k_set_rhop), 2 = gradient (k_grad_finalize), 3 = A <- 0.
+__global__ void k_batch_begin(const BatchImg* __restrict__ im, int k, int* queue)
+{
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        Accum* a = im[i].accum;
+        a->n_used = 0ull;
+        a->n_qclip = 0ull;
+        a->n_lclip = 0ull;
+        a->sum_logD = 0.0;
+        a->g_iz = 0.0;
+        a->g_il = 0.0;
+        a->sum_rhop = 0.0;
+        a->queue = 0;
+    }
+    if (threadIdx.x == 0) *queue = 0;
+}
+
+__global__ void k_batch_pixels(const BatchImg* __restrict__ im, int op)
+{
+    __shared__ double sh[kAuxThreads / 32];
+    const BatchImg b = im[blockIdx.y];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < b.npix; i += gridDim.x * blockDim.x) {
+        if (op == 0) {
+            const float r = b.rho[i] * b.A[i];
+            const float p = b.s[i] * r;
+            b.rho[i] = r;
+            b.rhop[i] = p;
+            b.A[i] = 0.0f;
+            acc += (double)p;
+        } else if (op == 1) {
+            const float p = b.s[i] * b.rho[i];
+            b.rhop[i] = p;
+            acc += (double)p;
+        } else if (op == 2) {
+            b.g[i] = b.s[i] * (b.A[i] - 1.0f);
+            b.A[i] = 0.0f;
+        } else {
+            b.A[i] = 0.0f;
+        }
+    }
+    if (op >= 2) return;
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) atomicAdd(&b.accum->sum_rhop, acc);
+}
+
 __global__ void k_fill(float* p, long long n, float v)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -367,6 +415,42 @@ cudaError_t launch_check_image(int n, const float* rho, int* bad, cudaStream_t s
 {
     k_check_image<<<blocks_for(n, kAuxThreads * 4, 1024), kAuxThreads, 0, st>>>(n, rho, bad);
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch_begin(const BatchImg* im, int k, int* queue, cudaStream_t st)
+{
+    k_batch_begin<<<1, kAuxThreads, 0, st>>>(im, k, queue);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_pixels(const BatchImg* im, int k, int max_npix, int op, cudaStream_t st)
+{
+    if (k <= 0) return cudaSuccess;
+    const dim3 grid(blocks_for(max_npix, kAuxThreads * 4, 256), k);
+    k_batch_pixels<<<grid, kAuxThreads, 0, st>>>(im, op);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_pass(int lmax, int mode, const BatchArgs& a, cudaStream_t st)
+{
+    switch (lmax) {
+    case 12: return launch_batch_pass_l<12>(mode, a, st);
+    case 24: return launch_batch_pass_l<24>(mode, a, st);
+    case 48: return launch_batch_pass_l<48>(mode, a, st);
+    case 64: return launch_batch_pass_l<64>(mode, a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t prepare_batch_pass(int lmax, size_t smem)
+{
+    switch (lmax) {
+    case 12: return prepare_batch_pass_l<12>(smem);
+    case 24: return prepare_batch_pass_l<24>(smem);
+    case 48: return prepare_batch_pass_l<48>(smem);
+    case 64: return prepare_batch_pass_l<64>(smem);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_pass(int lmax, int mode, const PassArgs& a, cudaStream_t st)

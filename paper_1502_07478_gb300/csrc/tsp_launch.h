@@ -26,16 +26,52 @@ struct PassArgs {
     size_t smem;       // dynamic shared memory of the tile kernel
 };
 
+// A batched pass: the tile items (bin, first, count, reconstruction) of every
+// reconstruction in `table`, in one persistent launch, and the outlier items
+// (-1, first, count, reconstruction) in a second launch when there are any.
+struct BatchArgs {
+    const Inst* table;
+    const int4* items;
+    int n_items;
+    const int4* outlier_items;
+    int n_outlier_items;
+    int* queue;        // work counter, zeroed before the launch
+    int nseg;
+    int grid;
+    size_t smem;
+};
+
+// Image buffers of one reconstruction of a batch, for the batched per-pixel
+// kernels.
+struct BatchImg {
+    float* rho;
+    float* rhop;
+    float* A;
+    const float* s;
+    float* g;          // gradient output (op 2)
+    Accum* accum;
+    int npix;
+    int pad;
+};
+
 // Tile kernel + outlier kernel of one pass (MODE = kMlem, kLoglik or kGrad).
 cudaError_t launch_pass(int lmax, int mode, const PassArgs& a, cudaStream_t st);
 // Raise the dynamic shared-memory limit of the tile kernel for (lmax, mode).
 cudaError_t prepare_pass(int lmax, int mode, size_t smem);
+
+// Batched pass (MODE = kMlem or kGrad) and its shared-memory limit.
+cudaError_t launch_batch_pass(int lmax, int mode, const BatchArgs& a, cudaStream_t st);
+cudaError_t prepare_batch_pass(int lmax, size_t smem);
 
 // Per-LMAX entry points (one translation unit each).
 template <int LMAX>
 cudaError_t launch_pass_l(int mode, const PassArgs& a, cudaStream_t st);
 template <int LMAX>
 cudaError_t prepare_pass_l(int mode, size_t smem);
+template <int LMAX>
+cudaError_t launch_batch_pass_l(int mode, const BatchArgs& a, cudaStream_t st);
+template <int LMAX>
+cudaError_t prepare_batch_pass_l(size_t smem);
 
 // Auxiliary kernels (tsp_kernels.cu).
 cudaError_t launch_sensitivity(double R, double L, int ny, int nz, double dy, double dz, float* s,
@@ -54,6 +90,8 @@ cudaError_t launch_finalize(int npix, float* rho, float* rhop, float* A, const f
 cudaError_t launch_grad_finalize(int npix, float* g, float* A, const float* s, cudaStream_t st);
 cudaError_t launch_set_rhop(int npix, const float* rho, const float* s, float* rhop, Accum* accum,
                             cudaStream_t st);
+cudaError_t launch_batch_begin(const BatchImg* im, int k, int* queue, cudaStream_t st);
+cudaError_t launch_batch_pixels(const BatchImg* im, int k, int max_npix, int op, cudaStream_t st);
 cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t st);
 cudaError_t launch_product(int npix, const float* a, const float* b, float* out, cudaStream_t st);
 cudaError_t launch_check_image(int npix, const float* rho, int* bad, cudaStream_t st);

@@ -451,83 +451,126 @@ __device__ __forceinline__ void flush_block_sums(const BlockSums* bs, Accum* acc
     }
 }
 
-// Persistent tile kernel.
-template <int LMAX, int MODE, int NSEG>
+// Frame of tile bin `bin` (the staged region of Tiling), or the whole image
+// for bin < 0 (the outlier path).
+__device__ __forceinline__ Frame tile_frame(const Geo& g, const Tiling& tl, int bin)
+{
+    Frame f;
+    if (bin < 0) {
+        f.oy = 0;
+        f.zbase = 0;
+        f.Y0 = 0;
+        f.stride = g.nz;
+        f.rh = g.ny;
+        f.rw = g.nz;
+        f.shear = 0.0f;
+        return f;
+    }
+    const int tiles_per_bin = tl.tiles_y * tl.tiles_z;
+    const int b = bin / tiles_per_bin;
+    const int rest = bin - b * tiles_per_bin;
+    const int ty = rest / tl.tiles_z, tz = rest - ty * tl.tiles_z;
+    f.oy = ty * tl.TY - tl.HY;
+    f.zbase = tz * tl.TZ - tl.HZ - tl.zs_off;
+    f.Y0 = tl.Y0;
+    f.stride = tl.RS;
+    f.rh = tl.RH;
+    f.rw = tl.RW;
+    f.shear = bin_shear(tl, b);
+    return f;
+}
+
+// Persistent tile kernel.  Work items are int4 (tile bin, first event, count,
+// reconstruction).  Plain form (BATCH = false): one reconstruction, passed as
+// `p`.  Batched form: item.w indexes `table`, whose record is copied to shared
+// memory when it changes.  `queue` is the work counter (zero at launch).
+template <int LMAX, int MODE, int NSEG, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1)
-k_tiles(Geo g, Tiling tl, EventsView evs, const int4* __restrict__ items, int n_items,
-        const float* __restrict__ rhop, float* __restrict__ A, Accum* accum, int G)
+k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, int n_items,
+        int* queue)
 {
     extern __shared__ float4 smem_f4[];
-    float* s_rp = reinterpret_cast<float*>(smem_f4) + kPadFloats;
-    const int region = tl.RH * tl.RS;
-    float* s_acc = s_rp + region + 2 * kPadFloats;
-    float* s_part = s_acc + region + kPadFloats;
+    float* const smem = reinterpret_cast<float*>(smem_f4);
     __shared__ int s_item;
     __shared__ Frame s_frame;
     __shared__ BlockSums s_sums;
+    __shared__ Inst s_inst;
+    const Inst& I = BATCH ? s_inst : p;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ngroups = kWarps / G;
-    const int grp = warp / G, wig = warp - grp * G;
-    float* part = s_part + grp * (2 * 3 * G);
-    int parity = 0;
     init_block_sums(&s_sums);
-
-    for (int k = tid; k < kPadFloats; k += kThreads) {
-        s_rp[-kPadFloats + k] = 0.0f;
-        s_rp[region + k] = 0.0f;
-        s_acc[-kPadFloats + k] = 0.0f;
-        s_acc[region + k] = 0.0f;
-    }
-
-    const int tiles_per_bin = tl.tiles_y * tl.tiles_z;
-    for (;;) {
-        if (tid == 0) {
-            const int it = atomicAdd(&accum->queue, 1);
-            s_item = it;
-            if (it < n_items) {
-                const int4 item = items[it];        // (bin, first event, count, 0)
-                const int b = item.x / tiles_per_bin;
-                const int rest = item.x - b * tiles_per_bin;
-                const int ty = rest / tl.tiles_z, tz = rest - (rest / tl.tiles_z) * tl.tiles_z;
-                s_frame.oy = ty * tl.TY - tl.HY;
-                s_frame.zbase = tz * tl.TZ - tl.HZ - tl.zs_off;
-                s_frame.Y0 = tl.Y0;
-                s_frame.stride = tl.RS;
-                s_frame.rh = tl.RH;
-                s_frame.rw = tl.RW;
-                s_frame.shear = bin_shear(tl, b);
-            }
+    if (!BATCH) {
+        const int region = p.tl.RH * p.tl.RS;
+        float* s_rp = smem + kPadFloats;
+        float* s_acc = s_rp + region + 2 * kPadFloats;
+        for (int k = tid; k < kPadFloats; k += kThreads) {
+            s_rp[-kPadFloats + k] = 0.0f;
+            s_rp[region + k] = 0.0f;
+            s_acc[-kPadFloats + k] = 0.0f;
+            s_acc[region + k] = 0.0f;
         }
+    }
+    int cur = -1;                                 // reconstruction held in s_inst
+
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(queue, 1);
         __syncthreads();
         const int it = s_item;
         if (it >= n_items) break;
         const int4 item = items[it];
-        {
-            const Frame f = s_frame;
-            for (int rr = warp; rr < tl.RH; rr += kWarps) {
-                const int iy = f.oy + rr;
-                const bool row_in = iy >= 0 && iy < g.ny;
-                const int z0row = f.zbase + (int)rintf(__fmul_rn(f.shear, (float)(iy - f.Y0)));
-                for (int cc = lane; cc < tl.RS; cc += 32) {
-                    const int iz = z0row + cc;
-                    float v = 0.0f;
-                    if (row_in && cc < tl.RW && iz >= 0 && iz < g.nz)
-                        v = rhop[(size_t)iy * g.nz + iz];
-                    s_rp[rr * tl.RS + cc] = v;
-                    if (MODE != kLoglik) s_acc[rr * tl.RS + cc] = 0.0f;
-                }
+        if (BATCH && item.w != cur) {
+            if (cur >= 0 && tid == 0) {
+                flush_block_sums(&s_sums, s_inst.accum, MODE);
+                init_block_sums(&s_sums);
+            }
+            __syncthreads();
+            const unsigned long long* src = reinterpret_cast<const unsigned long long*>(table + item.w);
+            unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s_inst);
+            for (int k = tid; k < (int)(sizeof(Inst) / 8); k += kThreads) dst[k] = src[k];
+            cur = item.w;
+            __syncthreads();
+            const int region = s_inst.tl.RH * s_inst.tl.RS;
+            float* s_rp = smem + kPadFloats;
+            float* s_acc = s_rp + region + 2 * kPadFloats;
+            for (int k = tid; k < kPadFloats; k += kThreads) {
+                s_rp[-kPadFloats + k] = 0.0f;
+                s_rp[region + k] = 0.0f;
+                s_acc[-kPadFloats + k] = 0.0f;
+                s_acc[region + k] = 0.0f;
+            }
+        }
+        const Geo& g = I.g;
+        const Tiling& tl = I.tl;
+        const int G = I.G;
+        const int ngroups = kWarps / G;
+        const int grp = warp / G, wig = warp - grp * G;
+        const int region = tl.RH * tl.RS;
+        float* s_rp = smem + kPadFloats;
+        float* s_acc = s_rp + region + 2 * kPadFloats;
+        float* part = s_acc + region + kPadFloats + grp * (2 * 3 * G);
+        int parity = 0;
+        const Frame f = tile_frame(g, tl, item.x);
+        if (tid == 0) s_frame = f;
+        for (int rr = warp; rr < tl.RH; rr += kWarps) {
+            const int iy = f.oy + rr;
+            const bool row_in = iy >= 0 && iy < g.ny;
+            const int z0row = f.zbase + (int)rintf(__fmul_rn(f.shear, (float)(iy - f.Y0)));
+            for (int cc = lane; cc < tl.RS; cc += 32) {
+                const int iz = z0row + cc;
+                float v = 0.0f;
+                if (row_in && cc < tl.RW && iz >= 0 && iz < g.nz)
+                    v = I.rhop[(size_t)iy * g.nz + iz];
+                s_rp[rr * tl.RS + cc] = v;
+                if (MODE != kLoglik) s_acc[rr * tl.RS + cc] = 0.0f;
             }
         }
         __syncthreads();
-        if (grp < ngroups) {
+        if (grp < ngroups)
             for (int e = item.y + grp; e < item.y + item.z; e += ngroups)
-                process_event<LMAX, MODE, NSEG, true>(g, evs, e, G, wig, lane, 1 + grp, part,
+                process_event<LMAX, MODE, NSEG, true>(g, I.evs, e, G, wig, lane, 1 + grp, part,
                                                       parity, &s_frame, s_rp, s_acc, &s_sums);
-        }
         __syncthreads();
         if (MODE != kLoglik) {
-            const Frame f = s_frame;
             for (int rr = warp; rr < tl.RH; rr += kWarps) {
                 const int iy = f.oy + rr;
                 if (iy < 0 || iy >= g.ny) continue;
@@ -535,14 +578,15 @@ k_tiles(Geo g, Tiling tl, EventsView evs, const int4* __restrict__ items, int n_
                 for (int cc = lane; cc < tl.RW; cc += 32) {
                     const int iz = z0row + cc;
                     const float v = s_acc[rr * tl.RS + cc];
-                    if (iz >= 0 && iz < g.nz && v != 0.0f) atomicAdd(A + (size_t)iy * g.nz + iz, v);
+                    if (iz >= 0 && iz < g.nz && v != 0.0f)
+                        atomicAdd(I.A + (size_t)iy * g.nz + iz, v);
                 }
             }
             __syncthreads();
         }
     }
     __syncthreads();
-    flush_block_sums(&s_sums, accum, MODE);
+    if (!BATCH || cur >= 0) flush_block_sums(&s_sums, I.accum, MODE);
 }
 
 // Events whose window does not fit their tile's region: same evaluation, with
@@ -578,6 +622,42 @@ k_outliers(Geo g, EventsView evs, int first, int count, const float* __restrict_
     }
     __syncthreads();
     flush_block_sums(&s_sums, accum, MODE);
+}
+
+// Batched outlier kernel: items (-1, first, count, reconstruction), one block
+// per item at a time.
+template <int LMAX, int MODE, int NSEG>
+__global__ void __launch_bounds__(kThreads, 1)
+k_outliers_batch(const Inst* __restrict__ table, const int4* __restrict__ items, int n_items)
+{
+    __shared__ float s_part[kWarps * 2 * 3];
+    __shared__ Frame s_frame;
+    __shared__ BlockSums s_sums;
+    __shared__ Inst s_inst;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int4 item = items[it];
+        __syncthreads();
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(table + item.w);
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(&s_inst);
+        for (int k = tid; k < (int)(sizeof(Inst) / 8); k += kThreads) dst[k] = src[k];
+        init_block_sums(&s_sums);
+        __syncthreads();
+        if (tid == 0) s_frame = tile_frame(s_inst.g, s_inst.tl, -1);
+        __syncthreads();
+        const int G = s_inst.G;
+        const int ngroups = kWarps / G;
+        const int grp = warp / G, wig = warp - grp * G;
+        float* part = s_part + grp * (2 * 3 * G);
+        int parity = 0;
+        if (grp < ngroups)
+            for (int k = grp; k < item.z; k += ngroups)
+                process_event<LMAX, MODE, NSEG, false>(s_inst.g, s_inst.evs, item.y + k, G, wig,
+                                                       lane, 1 + grp, part, parity, &s_frame,
+                                                       s_inst.rhop, s_inst.A, &s_sums);
+        __syncthreads();
+        flush_block_sums(&s_sums, s_inst.accum, MODE);
+    }
 }
 
 }  // namespace tsp

@@ -15,9 +15,19 @@ namespace {
 template <int LMAX, int MODE, int NSEG>
 cudaError_t run_pass(const PassArgs& a, cudaStream_t st)
 {
-    if (a.n_items > 0)
-        k_tiles<LMAX, MODE, NSEG><<<a.grid, kThreads, a.smem, st>>>(
-            a.g, a.tl, a.evs, a.items, a.n_items, a.rhop, a.A, a.accum, a.G);
+    if (a.n_items > 0) {
+        Inst p;
+        p.g = a.g;
+        p.tl = a.tl;
+        p.evs = a.evs;
+        p.rhop = a.rhop;
+        p.A = a.A;
+        p.accum = a.accum;
+        p.G = a.G;
+        p.pad = 0;
+        k_tiles<LMAX, MODE, NSEG, false><<<a.grid, kThreads, a.smem, st>>>(
+            p, nullptr, a.items, a.n_items, &a.accum->queue);
+    }
     if (a.outlier_count > 0) {
         const int per_block = kWarps / a.G;
         int blocks = (a.outlier_count + per_block - 1) / per_block;
@@ -31,8 +41,45 @@ cudaError_t run_pass(const PassArgs& a, cudaStream_t st)
 template <int LMAX, int MODE, int NSEG>
 cudaError_t set_smem(size_t smem)
 {
-    return cudaFuncSetAttribute(k_tiles<LMAX, MODE, NSEG>,
+    return cudaFuncSetAttribute(k_tiles<LMAX, MODE, NSEG, false>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+// Batched form: one persistent launch over the items of every reconstruction
+// (MLEM and gradient passes).
+template <int LMAX, int MODE, int NSEG>
+cudaError_t run_batch(const BatchArgs& a, cudaStream_t st)
+{
+    Inst none{};
+    if (a.n_items > 0)
+        k_tiles<LMAX, MODE, NSEG, true><<<a.grid, kThreads, a.smem, st>>>(none, a.table, a.items,
+                                                                          a.n_items, a.queue);
+    if (a.n_outlier_items > 0)
+        k_outliers_batch<LMAX, MODE, NSEG>
+            <<<a.n_outlier_items < a.grid ? a.n_outlier_items : a.grid, kThreads, 0, st>>>(
+                a.table, a.outlier_items, a.n_outlier_items);
+    return cudaGetLastError();
+}
+
+template <int LMAX, int NSEG>
+cudaError_t run_batch_mode(int mode, const BatchArgs& a, cudaStream_t st)
+{
+    switch (mode) {
+    case kMlem: return run_batch<LMAX, kMlem, NSEG>(a, st);
+    case kGrad: return run_batch<LMAX, kGrad, NSEG>(a, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int LMAX, int NSEG>
+cudaError_t batch_smem(size_t smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_tiles<LMAX, kMlem, NSEG, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tiles<LMAX, kGrad, NSEG, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
 }
 
 template <int LMAX, int NSEG>
@@ -70,6 +117,21 @@ cudaError_t prepare_pass_l<TSP_LMAX>(int mode, size_t smem)
 {
     cudaError_t e = smem_mode<TSP_LMAX, 1>(mode, smem);
     if (e == cudaSuccess) e = smem_mode<TSP_LMAX, 2>(mode, smem);
+    return e;
+}
+
+template <>
+cudaError_t launch_batch_pass_l<TSP_LMAX>(int mode, const BatchArgs& a, cudaStream_t st)
+{
+    return a.nseg == 1 ? run_batch_mode<TSP_LMAX, 1>(mode, a, st)
+                       : run_batch_mode<TSP_LMAX, 2>(mode, a, st);
+}
+
+template <>
+cudaError_t prepare_batch_pass_l<TSP_LMAX>(size_t smem)
+{
+    cudaError_t e = batch_smem<TSP_LMAX, 1>(smem);
+    if (e == cudaSuccess) e = batch_smem<TSP_LMAX, 2>(smem);
     return e;
 }
 

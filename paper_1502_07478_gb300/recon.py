@@ -99,6 +99,31 @@ class Recon:
             raise ValueError("zu, zd, dl must have the same length")
         self._chk(self._lib.tsp_upload_events(self._h, pu, pd, pl, n, du, _stream_handle(stream)))
 
+    def begin_events(self, n_total: int, stream=None):
+        """Start a streamed upload of n_total events (tsp_begin_events)."""
+        self._chk(self._lib.tsp_begin_events(self._h, int(n_total), _stream_handle(stream)))
+        self._pending = []
+
+    def append_events(self, zu, zd, dl, stream=None):
+        """Append one chunk (host arrays, pinned CPU tensors or CUDA tensors).
+        The chunk is kept alive until end_events, since the copy may still be
+        in flight when this returns."""
+        pu, du, ku = _arg(zu)
+        pd, dd, kd = _arg(zd)
+        pl, dl_, kl = _arg(dl)
+        if not (du == dd == dl_):
+            raise ValueError("zu, zd, dl must all be host arrays or all be CUDA tensors")
+        n = int(ku.numel() if du else ku.size)
+        if (kd.numel() if dd else kd.size) != n or (kl.numel() if dl_ else kl.size) != n:
+            raise ValueError("zu, zd, dl must have the same length")
+        self._chk(self._lib.tsp_append_events(self._h, pu, pd, pl, n, du, _stream_handle(stream)))
+        getattr(self, "_pending", []).append((ku, kd, kl, zu, zd, dl))
+
+    def end_events(self, stream=None):
+        """Bin the appended events (tsp_end_events; synchronises)."""
+        self._chk(self._lib.tsp_end_events(self._h, _stream_handle(stream)))
+        self._pending = []
+
     def compute_sensitivity(self, out=None, stream=None):
         """Sensitivity map (Eq. s-yz) as a CUDA tensor (or into ``out``)."""
         if out is None:
@@ -166,12 +191,188 @@ class Recon:
     def set_profiling(self, on: bool = True):
         self._chk(self._lib.tsp_set_profiling(self._h, int(bool(on))))
 
+    @property
+    def schedule(self) -> dict:
+        s = L.Schedule()
+        self._chk(self._lib.tsp_get_schedule(self._h, C.byref(s)))
+        return _sched_dict(s)
+
+    def set_schedule(self, ty_cap: int = 128, items_per_sm: int = 8, order: int = 0, stream=None):
+        s = L.Schedule(int(ty_cap), int(items_per_sm), int(order), 0)
+        self._chk(self._lib.tsp_set_schedule(self._h, C.byref(s), _stream_handle(stream)))
+
+    def autotune(self, stream=None) -> Tuple[dict, float]:
+        """Pick the fastest tile schedule by timing MLEM passes; returns
+        (schedule, pass ms)."""
+        s = L.Schedule()
+        ms = C.c_float()
+        self._chk(self._lib.tsp_autotune(self._h, C.byref(s), C.byref(ms), _stream_handle(stream)))
+        return _sched_dict(s), ms.value
+
     def pass_times(self, max_count: int = 4096, stream=None):
         """Device durations (ms) of the MLEM kernel launches of the last iterate."""
         buf = (C.c_float * max_count)()
         cnt = C.c_int()
         self._chk(self._lib.tsp_pass_times(self._h, buf, max_count, C.byref(cnt),
                                            _stream_handle(stream)))
+        return [buf[i] for i in range(cnt.value)]
+
+
+def _sched_dict(s) -> dict:
+    return {"ty_cap": s.ty_cap, "items_per_sm": s.items_per_sm, "order": s.order}
+
+
+def _params(R, L_, ny, nz, sigma_z, sigma_dl, cut=3.0, dy=0.0, dz=0.0):
+    return L.Params(float(R), float(L_), int(ny), int(nz), float(dy), float(dz), float(sigma_z),
+                    float(sigma_dl), float(cut), 0, 0)
+
+
+class Batch:
+    """k independent reconstructions advanced together (tsp_batch_*): one
+    persistent tile launch per iteration over the work of all of them.
+
+    ``params`` is a sequence of dicts with the keys of ``Recon`` (R, L, ny, nz,
+    sigma_z, sigma_dl, optionally cut, dy, dz) or of workload objects."""
+
+    def __init__(self, params, device: Optional[int] = None):
+        self._lib = L.lib()
+        if torch is not None and torch.cuda.is_available():
+            if device is not None:
+                torch.cuda.set_device(device)
+            torch.cuda.init()
+        plist = []
+        for p in params:
+            if not isinstance(p, dict):
+                p = dict(R=p.R, L=p.L, ny=p.ny, nz=p.nz, sigma_z=p.sigma_z,
+                         sigma_dl=p.sigma_dl, cut=p.cut)
+            plist.append(_params(p["R"], p["L"], p["ny"], p["nz"], p["sigma_z"], p["sigma_dl"],
+                                 p.get("cut", 3.0), p.get("dy", 0.0), p.get("dz", 0.0)))
+        if not plist:
+            raise ValueError("a batch needs at least one reconstruction")
+        self.params = (L.Params * len(plist))(*plist)
+        self.shapes = [(p.ny, p.nz) for p in plist]
+        h = C.c_void_p()
+        rc = self._lib.tsp_batch_create(self.params, len(plist), C.byref(h))
+        L.check_batch(None, rc)
+        self._h = h
+
+    @classmethod
+    def from_workloads(cls, ws, **kw):
+        return cls(list(ws), **kw)
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.tsp_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _chk(self, rc):
+        L.check_batch(self._h, rc)
+
+    def upload_events(self, i: int, zu, zd, dl, stream=None):
+        pu, du, ku = _arg(zu)
+        pd, dd, kd = _arg(zd)
+        pl, dl_, kl = _arg(dl)
+        if not (du == dd == dl_):
+            raise ValueError("zu, zd, dl must all be host arrays or all be CUDA tensors")
+        n = int(ku.numel() if du else ku.size)
+        if (kd.numel() if dd else kd.size) != n or (kl.numel() if dl_ else kl.size) != n:
+            raise ValueError("zu, zd, dl must have the same length")
+        self._chk(self._lib.tsp_batch_upload_events(self._h, int(i), pu, pd, pl, n, du,
+                                                    _stream_handle(stream)))
+
+    def set_image(self, i: int, rho=None, stream=None):
+        if rho is None:
+            self._chk(self._lib.tsp_batch_set_image(self._h, int(i), None, 0,
+                                                    _stream_handle(stream)))
+            return
+        p, dev, keep = _arg(rho)
+        ny, nz = self.shapes[i]
+        if (keep.numel() if dev else keep.size) != ny * nz:
+            raise ValueError("image must have ny*nz elements")
+        self._chk(self._lib.tsp_batch_set_image(self._h, int(i), p, dev, _stream_handle(stream)))
+
+    def set_sigma(self, i: int, sigma_z: float, sigma_dl: float, stream=None):
+        self._chk(self._lib.tsp_batch_set_sigma(self._h, int(i), float(sigma_z), float(sigma_dl),
+                                                _stream_handle(stream)))
+        self.params[i].sigma_z = float(sigma_z)
+        self.params[i].sigma_dl = float(sigma_dl)
+
+    def iterate(self, n_iter: int, stream=None):
+        self._chk(self._lib.tsp_batch_iterate(self._h, int(n_iter), _stream_handle(stream)))
+
+    def read_image(self, i: int, which: int = 0, out=None, stream=None):
+        """rho (0), rho' (1) or the last g_rho (2) of reconstruction i, as a
+        CUDA tensor or into ``out`` (CUDA tensor or NumPy array)."""
+        ny, nz = self.shapes[i]
+        if out is None:
+            out = torch.empty(ny, nz, dtype=torch.float32, device="cuda")
+        if isinstance(out, np.ndarray):
+            if out.dtype != np.float32 or not out.flags.c_contiguous or out.size != ny * nz:
+                raise ValueError("out must be a contiguous float32 array of ny*nz elements")
+            self._chk(self._lib.tsp_batch_read_image(self._h, int(i), C.c_void_p(out.ctypes.data),
+                                                     int(which), 0, _stream_handle(stream)))
+            return out
+        p, dev, keep = _arg(out)
+        if keep is not out:
+            raise ValueError("out must be a contiguous float32 CUDA tensor")
+        self._chk(self._lib.tsp_batch_read_image(self._h, int(i), p, int(which), dev,
+                                                 _stream_handle(stream)))
+        return out
+
+    def loglik_grad(self, stream=None):
+        """(L, g_sigma): arrays of shape (k,) and (k, 2); g_rho of
+        reconstruction i is ``read_image(i, which=2)``."""
+        k = len(self)
+        Lv = (C.c_double * k)()
+        gs = (C.c_double * (2 * k))()
+        self._chk(self._lib.tsp_batch_loglik_grad(self._h, Lv, gs, _stream_handle(stream)))
+        return np.array(Lv[:]), np.array(gs[:]).reshape(k, 2)
+
+    def stats(self, i: int, stream=None) -> dict:
+        s = L.Stats()
+        self._chk(self._lib.tsp_batch_stats(self._h, int(i), C.byref(s), _stream_handle(stream)))
+        return {k: getattr(s, k) for k, _ in L.Stats._fields_}
+
+    @property
+    def schedule(self) -> dict:
+        s = L.Schedule()
+        self._chk(self._lib.tsp_batch_get_schedule(self._h, C.byref(s)))
+        return _sched_dict(s)
+
+    def set_schedule(self, ty_cap: int = 128, items_per_sm: int = 8, order: int = 0, stream=None):
+        s = L.Schedule(int(ty_cap), int(items_per_sm), int(order), 0)
+        self._chk(self._lib.tsp_batch_set_schedule(self._h, C.byref(s), _stream_handle(stream)))
+
+    def autotune(self, stream=None) -> Tuple[dict, float]:
+        s = L.Schedule()
+        ms = C.c_float()
+        self._chk(self._lib.tsp_batch_autotune(self._h, C.byref(s), C.byref(ms),
+                                               _stream_handle(stream)))
+        return _sched_dict(s), ms.value
+
+    def set_profiling(self, on: bool = True):
+        self._chk(self._lib.tsp_batch_set_profiling(self._h, int(bool(on))))
+
+    def pass_times(self, max_count: int = 4096, stream=None):
+        buf = (C.c_float * max_count)()
+        cnt = C.c_int()
+        self._chk(self._lib.tsp_batch_pass_times(self._h, buf, max_count, C.byref(cnt),
+                                                 _stream_handle(stream)))
         return [buf[i] for i in range(cnt.value)]
 
 

@@ -9,10 +9,10 @@ reconstruction, no kernel, no sensitivity, no MLEM update).
 """
 from .phantom import Ellipse, Phantom, paper_phantom, random_phantom
 from .events import Geometry, simulate_events
-from .configs import WORKLOADS, Workload, make_workload
+from .configs import WORKLOADS, Workload, batched_instances, make_workload
 
 __all__ = [
     "Ellipse", "Phantom", "paper_phantom", "random_phantom",
     "Geometry", "simulate_events",
-    "WORKLOADS", "Workload", "make_workload",
+    "WORKLOADS", "Workload", "batched_instances", "make_workload",
 ]

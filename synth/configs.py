@@ -53,6 +53,22 @@ class Workload:
         return simulate_events(self.phantom(), self.geometry, self.n_events, self.seed,
                                dtype=dtype)
 
+    def chunk_sizes(self, chunk: int):
+        return [min(chunk, self.n_events - f) for f in range(0, self.n_events, chunk)]
+
+    def event_chunk(self, k: int, chunk: int, dtype=np.float32):
+        """Chunk k (of chunk_sizes(chunk)) of the streamed form of the event set:
+        chunk k is drawn from the seed sequence (seed, k), so chunks can be made
+        independently and in parallel.  (A different event set from events(),
+        with the same distribution.)"""
+        n = self.chunk_sizes(chunk)[k]
+        return simulate_events(self.phantom(), self.geometry, n, (self.seed, k), dtype=dtype)
+
+    def event_chunks(self, chunk: int = 10_000_000, dtype=np.float32):
+        """Iterate over the chunks of the streamed event set."""
+        for k in range(len(self.chunk_sizes(chunk))):
+            yield self.event_chunk(k, chunk, dtype)
+
 
 def _small_phantom():
     rng = np.random.Generator(np.random.PCG64(1001))

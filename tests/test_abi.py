@@ -43,6 +43,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_layouts_match_header():
     assert C.sizeof(L.Params) == 8 * 2 + 4 * 2 + 8 * 5 + 4 * 2
     assert C.sizeof(L.Stats) == 8 * 10
+    assert C.sizeof(L.Schedule) == 4 * 4
 
 
 def test_version(lib):
@@ -75,3 +76,27 @@ def test_null_arguments(lib):
     lib.tsp_destroy(None)
     assert lib.tsp_iterate(None, 1, None) == L.TSP_EINVAL
     assert lib.tsp_upload_events(None, None, None, None, 0, 0, None) == L.TSP_EINVAL
+
+
+def test_batch_rejects_bad_params(lib):
+    h = C.c_void_p(123)
+    ps = (L.Params * 3)(_params(), _params(ny=0), _params())
+    assert lib.tsp_batch_create(ps, 3, C.byref(h)) == L.TSP_EINVAL
+    assert h.value is None
+    assert b"reconstruction 1" in lib.tsp_batch_last_error(None)
+    assert lib.tsp_batch_create(ps, 0, C.byref(h)) == L.TSP_EINVAL
+    assert lib.tsp_batch_create(None, 2, C.byref(h)) == L.TSP_EINVAL
+    assert lib.tsp_batch_create(ps, 1, None) == L.TSP_EINVAL
+
+
+def test_batch_null_arguments(lib):
+    lib.tsp_batch_destroy(None)
+    assert lib.tsp_batch_size(None) == 0
+    assert lib.tsp_batch_iterate(None, 1, None) == L.TSP_EINVAL
+    assert lib.tsp_batch_upload_events(None, 0, None, None, None, 0, 0, None) == L.TSP_EINVAL
+    assert lib.tsp_batch_loglik_grad(None, None, None, None) == L.TSP_EINVAL
+    assert lib.tsp_batch_autotune(None, None, None, None) == L.TSP_EINVAL
+    s = L.Schedule(128, 8, 0, 0)
+    assert lib.tsp_batch_set_schedule(None, C.byref(s), None) == L.TSP_EINVAL
+    assert lib.tsp_set_schedule(None, C.byref(s), None) == L.TSP_EINVAL
+    assert lib.tsp_autotune(None, None, None, None) == L.TSP_EINVAL

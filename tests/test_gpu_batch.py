@@ -1,0 +1,264 @@
+"""GPU parity of the batched path (tsp_batch_*): k reconstructions with their
+own grids, resolutions and event counts advanced by one persistent tile launch
+per iteration must match the FP64 oracle per reconstruction (max relative
+error <= 1e-4 on pixels above 1% of the maximum) and the plain per-context path.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Setup
+from synth import batched_instances, make_workload
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def rel_err(gpu, ref, frac=0.01):
+    gpu = np.asarray(gpu, dtype=np.float64).reshape(ref.shape)
+    mask = ref > frac * ref.max()
+    return float(np.max(np.abs(gpu[mask] - ref[mask]) / ref[mask]))
+
+
+def _instances(k=6, n_max=20_000):
+    ws = batched_instances(64, seed=3)[:k]
+    return [dataclasses.replace(w, n_events=min(w.n_events, n_max)) for w in ws]
+
+
+@pytest.fixture(scope="module")
+def mixed():
+    """Six instances of the batched workload (1, 2 and 4 mm pixels, sigma_z 8-12,
+    sigma_dl 30-50), at most 2e4 events each, plus their events."""
+    ws = _instances()
+    return ws, [w.events() for w in ws]
+
+
+def _batch(ws, evs):
+    from paper_1502_07478_gb300 import Batch
+    b = Batch.from_workloads(ws)
+    for i, ev in enumerate(evs):
+        b.upload_events(i, *ev)
+    return b
+
+
+def _images(b, ws, which=0):
+    return [b.read_image(i, which, out=np.empty((w.ny, w.nz), np.float32))
+            for i, w in enumerate(ws)]
+
+
+def test_batch_matches_oracle(mixed):
+    ws, evs = mixed
+    assert len({w.dz for w in ws}) > 1, "the fixture should mix pixel sizes"
+    b = _batch(ws, evs)
+    b.iterate(5)
+    imgs = _images(b, ws)
+    for i, (w, ev) in enumerate(zip(ws, evs)):
+        ref, rst = oracle.mlem(Setup.from_workload(w), ev, 5)
+        st = b.stats(i)
+        assert rel_err(imgs[i], ref) <= TOL, (i, w)
+        assert st["n_used"] == rst.n_used
+        assert st["n_clipped"] == 0 and st["n_qbad"] == 0
+        assert st["iterations"] == 5
+    b.close()
+
+
+def test_batch_matches_plain_contexts(mixed):
+    from paper_1502_07478_gb300 import Recon
+    ws, evs = mixed
+    b = _batch(ws, evs)
+    b.iterate(3)
+    imgs = _images(b, ws)
+    for i, (w, ev) in enumerate(zip(ws, evs)):
+        r = Recon.from_workload(w)
+        r.upload_events(*ev)
+        r.iterate(3)
+        plain = r.read_image(out=np.empty((w.ny, w.nz), np.float32))
+        r.close()
+        assert rel_err(imgs[i], plain.astype(np.float64)) <= 1e-5
+    b.close()
+
+
+def test_iterations_split_and_launch_count(mixed):
+    """2 + 3 iterations equal 5; each iteration is 3 launches for the batch
+    (reset, one persistent tile pass, image update) when no event is an outlier."""
+    ws, evs = mixed
+    b1 = _batch(ws, evs)
+    b1.iterate(5)
+    b2 = _batch(ws, evs)
+    b2.iterate(2)
+    before = b2.stats(0)["launches"]
+    b2.iterate(3)
+    after = b2.stats(0)["launches"]
+    if all(b2.stats(i)["n_outliers"] == 0 for i in range(len(ws))):
+        assert after - before == 3 * 3
+    # the work queue hands items to blocks in a run-dependent order, so the
+    # float sums agree to rounding only
+    for x, y in zip(_images(b1, ws), _images(b2, ws)):
+        assert rel_err(y, x.astype(np.float64)) <= 1e-5
+    b1.close()
+    b2.close()
+
+
+@pytest.mark.parametrize("sched", [dict(ty_cap=16, items_per_sm=2, order=1),
+                                   dict(ty_cap=64, items_per_sm=32, order=0)])
+def test_schedule_does_not_change_results(mixed, sched):
+    ws, evs = mixed
+    b = _batch(ws, evs)
+    b.iterate(3)
+    ref = _images(b, ws)
+    b2 = _batch(ws, evs)
+    b2.set_schedule(**sched)
+    assert b2.schedule == sched
+    b2.iterate(3)
+    for x, y in zip(ref, _images(b2, ws)):
+        assert rel_err(y, x.astype(np.float64)) <= 1e-5
+    b.close()
+    b2.close()
+
+
+def test_autotune_keeps_images(mixed):
+    ws, evs = mixed
+    b = _batch(ws, evs)
+    b.iterate(2)
+    before = _images(b, ws)
+    s_before = [b.stats(i)["sum_s_rho"] for i in range(len(ws))]
+    sched, ms = b.autotune()
+    assert ms > 0
+    assert 4 <= sched["ty_cap"] <= 128 and 1 <= sched["items_per_sm"] <= 64
+    assert sched == b.schedule
+    for x, y in zip(before, _images(b, ws)):
+        np.testing.assert_array_equal(x, y)     # the trials leave rho untouched
+    for i in range(len(ws)):
+        assert b.stats(i)["sum_s_rho"] == pytest.approx(s_before[i], rel=1e-6)
+    b.iterate(1)      # still iterates after the trials
+    b.close()
+
+
+def test_batch_loglik_grad_matches_plain(mixed):
+    from paper_1502_07478_gb300 import Recon
+    ws, evs = mixed
+    b = _batch(ws, evs)
+    b.iterate(2)
+    for i, w in enumerate(ws):
+        b.set_sigma(i, 1.3 * w.sigma_z, 1.25 * w.sigma_dl)
+    Lb, gsb = b.loglik_grad()
+    for i, (w, ev) in enumerate(zip(ws, evs)):
+        rho = b.read_image(i)
+        r = Recon.from_workload(w)
+        r.upload_events(*ev)
+        r.set_sigma(1.3 * w.sigma_z, 1.25 * w.sigma_dl)
+        r.set_image(rho)
+        Lp, gp, gsp = r.loglik_grad()
+        gb = b.read_image(i, which=2)
+        assert Lb[i] == pytest.approx(Lp, rel=1e-6)
+        assert float((gb - gp).norm() / gp.norm()) <= 1e-5
+        np.testing.assert_allclose(gsb[i], gsp, rtol=1e-4)
+        r.close()
+    b.close()
+
+
+def test_batch_gradient_matches_oracle():
+    """One adjoint instance in a batch of two, against the FP64 oracle at
+    sigma = (14, 55)."""
+    w = make_workload("adjoint_2mm", n_events=50_000)
+    w2 = make_workload("small_5mm")
+    ev, ev2 = w.events(), w2.events()
+    b = _batch([w, w2], [ev, ev2])
+    b.iterate(3)
+    rho = b.read_image(0).cpu().numpy().astype(np.float64)
+    b.set_sigma(0, 14.0, 55.0)
+    Lb, gsb = b.loglik_grad()
+    g = b.read_image(0, which=2).cpu().numpy().astype(np.float64)
+    Lref, gref, gsref = oracle.loglik_grad(Setup.from_workload(w, sigma_z=14.0, sigma_dl=55.0),
+                                           ev, rho)
+    assert Lb[0] == pytest.approx(Lref, rel=1e-6)
+    assert np.linalg.norm(g - gref) / np.linalg.norm(gref) <= 1e-4
+    np.testing.assert_allclose(gsb[0], gsref, rtol=1e-3)
+    b.close()
+
+
+def test_outliers_and_empty_instances_in_a_batch():
+    """An instance whose steep events take the batched outlier kernel, and an
+    instance with no events, next to an ordinary one."""
+    w = make_workload("small_5mm", n_events=3000)
+    zu, zd, dl = w.events()
+    rng = np.random.default_rng(8)
+    k = 600
+    y = rng.uniform(-150, 150, k)
+    z = rng.uniform(-100, 100, k)
+    t = rng.uniform(1.2, 2.0, k) * rng.choice([-1, 1], k)
+    ev_out = (np.concatenate([zu, (z + (350 - y) * t).astype(np.float32)]),
+              np.concatenate([zd, (z - (350 + y) * t).astype(np.float32)]),
+              np.concatenate([dl, (-2 * y * np.sqrt(1 + t * t)).astype(np.float32)]))
+    e = np.zeros(0, np.float32)
+    w2 = make_workload("adjoint_2mm", n_events=20_000)
+    ev2 = w2.events()
+    ws = [w, w, w2]
+    b = _batch(ws, [ev_out, (e, e, e), ev2])
+    b.iterate(3)
+    imgs = _images(b, ws)
+    assert b.stats(0)["n_outliers"] > 0
+    ref, _ = oracle.mlem(Setup.from_workload(w), ev_out, 3)
+    assert rel_err(imgs[0], ref) <= TOL
+    assert b.stats(1)["n_events"] == 0 and np.all(imgs[1] == 0.0)
+    ref2, _ = oracle.mlem(Setup.from_workload(w2), ev2, 3)
+    assert rel_err(imgs[2], ref2) <= TOL
+    b.close()
+
+
+def test_iterate_before_upload_is_a_state_error():
+    from paper_1502_07478_gb300 import Batch, TspError
+    from paper_1502_07478_gb300._lib import TSP_ESTATE, TSP_EINVAL
+    w = make_workload("small_5mm")
+    b = Batch.from_workloads([w, w])
+    b.upload_events(0, *w.events())
+    with pytest.raises(TspError) as ei:
+        b.iterate(1)
+    assert ei.value.code == TSP_ESTATE
+    with pytest.raises(TspError) as ei:
+        b.set_sigma(2, 10.0, 40.0)
+    assert ei.value.code == TSP_EINVAL
+    with pytest.raises(TspError) as ei:
+        b.set_schedule(ty_cap=2)
+    assert ei.value.code == TSP_EINVAL
+    b.close()
+
+
+def test_many_live_contexts_with_different_tiles():
+    """Contexts alive at the same time with different tile sizes (the kernel's
+    shared-memory limit is shared by all of them), iterated in any order."""
+    from paper_1502_07478_gb300 import Recon
+    ws = _instances(k=6, n_max=5_000)
+    rs = []
+    for w in ws:
+        r = Recon.from_workload(w)
+        r.upload_events(*w.events())
+        rs.append(r)
+    for r in reversed(rs):
+        r.iterate(2)
+    for r, w in zip(rs, ws):
+        assert r.stats()["n_used"] > 0
+        r.close()
+
+
+def test_plain_schedule_and_autotune():
+    from paper_1502_07478_gb300 import Recon
+    w = make_workload("adjoint_2mm", n_events=100_000)
+    ev = w.events()
+    r = Recon.from_workload(w)
+    r.upload_events(*ev)
+    r.iterate(2)
+    ref = r.read_image().cpu().numpy()
+    sched, ms = r.autotune()
+    assert ms > 0 and sched == r.schedule
+    np.testing.assert_array_equal(r.read_image().cpu().numpy(), ref)
+    r2 = Recon.from_workload(w)
+    r2.set_schedule(ty_cap=16, items_per_sm=2)
+    r2.upload_events(*ev)
+    r2.iterate(2)
+    assert rel_err(r2.read_image().cpu().numpy(), ref.astype(np.float64)) <= 1e-5
+    r.close()
+    r2.close()
