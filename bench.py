@@ -42,6 +42,10 @@ METRIC = "MLEM event-iterations/s (1e7 events, 1 mm grid), batched vs plain, rel
 UNIT = "event-iterations/s"
 MUFU_PER_PIXEL = 2          # one rsqrt and one ex2 per in-window pixel (pass 1)
 MUFU_PER_SM_CLK = 16        # SFU results per SM per clock (sm_100-class)
+# DRAM bytes per event of one MLEM tile pass (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch over 1e6 events of the 1 mm workload,
+# profiles/k_tiles_paper_1mm_1e6.md); the traffic grows with the events.
+TILE_PASS_DRAM_B_PER_EVENT = 40.0
 
 
 def _peaks():
@@ -279,8 +283,9 @@ def _make_chunk(args):
 
 
 def _make_events(args):
-    w = args
-    return w.events()
+    name, seed = args
+    from synth import make_workload
+    return make_workload(name, seed=seed).events()
 
 
 def bench_stress(args, workload, chunk: int = 10_000_000):
@@ -298,7 +303,7 @@ def bench_stress(args, workload, chunk: int = 10_000_000):
                                 mp_context=mp.get_context("spawn")) as ex:
         chunks = list(ex.map(_make_chunk, [(workload.name, workload.n_events, k, chunk)
                                            for k in range(len(sizes))]))
-        adj_ev = list(ex.map(_make_events, adj))
+        adj_ev = list(ex.map(_make_events, [("adjoint_2mm", w.seed) for w in adj]))
     import torch
     from paper_1502_07478_gb300 import Batch, Recon
     torch.cuda.set_device(0)
@@ -524,7 +529,10 @@ def main():
     achieved = W / t_pass if pass_ms else None
     roofline = {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
                 "peak": peak / 1e9, "unit": "Gpixel-evals/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": None,
+                "frac": (achieved / peak) if achieved else None,
+                "traffic": (TILE_PASS_DRAM_B_PER_EVENT * n
+                            if workload.name == "paper_1mm" and workload.dz == 1.0 else None),
+                "traffic_basis": "ncu DRAM bytes of one 1e6-event launch, scaled by events",
                 "kernel": "k_tiles (MLEM pass, per launch)", "pixel_evals_per_launch": W,
                 "launch_ms": t_pass * 1e3,
                 "peak_basis": f"{sms} SMs x {f_max/1e6:.0f} MHz x {MUFU_PER_SM_CLK} SFU ops/clk"
