@@ -405,7 +405,7 @@ def bench_stress(args, workload, chunk: int = 10_000_000):
         "roofline": {"bound": "alu", "achieved": W / t_pass / 1e9 if pass_ms else None,
                      "peak": peak / 1e9, "unit": "Gpixel-evals/s",
                      "frac": (W / t_pass / peak) if pass_ms else None, "traffic": None,
-                     "kernel": "MLEM pass (global-memory path), per launch",
+                     "kernel": "k_tiles (accumulator-only tiles, rho' from global), per launch",
                      "pixel_evals_per_launch": W, "launch_ms": t_pass * 1e3},
         "cpu_baseline": cpu,
         "e2e": {"value": n * n_iter / t_e2e, "unit": UNIT,

@@ -149,18 +149,40 @@ int plan(tsp_ctx* c)
     tl.TZ = RS - 2 * tl.HZ;
     const size_t budget = 200 * 1024;
     int TY = std::max(4, std::min(128, c->sched.ty_cap) / 4 * 4);
+    const int ty0 = TY;
     while (TY > 4 && tiles_smem_floats(TY + 2 * tl.HY, RS) * sizeof(float) > budget) TY -= 4;
+    c->gld = 0;
     if (tiles_smem_floats(TY + 2 * tl.HY, RS) * sizeof(float) > budget) {
-        // windows too large for a staged tile (very fine grids): no angle bins,
-        // so every event takes the global-memory path
-        tl.nb = 0;
-        TY = 4;
+        // windows too large to stage rho' and the accumulator (very fine
+        // grids): stage only the accumulator and read rho' from global memory,
+        // with two lanes per row; if even that does not fit, no angle bins, so
+        // every event takes the global-memory path
+        TY = ty0;
+        while (TY > 4 && tiles_acc_smem_floats(TY + 2 * tl.HY, RS) * sizeof(float) > budget)
+            TY -= 4;
+        if (tiles_acc_smem_floats(TY + 2 * tl.HY, RS) * sizeof(float) <= budget) {
+            c->gld = 1;
+            int l2 = 0;
+            for (int k = 0; k < kLmaxCount && !l2; ++k)
+                if (kLmaxList[k] >= need / 2 + 2) l2 = kLmaxList[k];
+            if (!l2) return fail(c, TSP_EINVAL, "window chords too long for the lane capacities");
+            c->lmax = l2;
+            c->nseg = 2;
+            c->G = 2 * ((maxrows + 31) / 32);
+            if (c->G > kWarps)
+                return fail(c, TSP_EINVAL, "window has more rows than one block can hold");
+        } else {
+            tl.nb = 0;
+            TY = 4;
+        }
     }
     tl.TY = std::min(TY, std::max(p.ny, 4));
     tl.RH = tl.TY + 2 * tl.HY;
     tl.tiles_y = (p.ny + tl.TY - 1) / tl.TY;
     tl.tiles_z = (p.nz + 2 * tl.zs_off + tl.TZ - 1) / tl.TZ;
-    c->smem = tl.nb > 0 ? tiles_smem_floats(tl.RH, tl.RS) * sizeof(float) : 0;
+    c->smem = tl.nb == 0 ? 0
+              : (c->gld ? tiles_acc_smem_floats(tl.RH, tl.RS) : tiles_smem_floats(tl.RH, tl.RS)) *
+                    sizeof(float);
     c->nbins = tl.nb * tl.tiles_y * tl.tiles_z + 1;
     // The dynamic shared-memory limit is a property of the kernel function,
     // shared by every context: raise it to the device's opt-in maximum (never
@@ -227,6 +249,7 @@ PassArgs pass_args(tsp_ctx* c)
     a.accum = c->accum;
     a.G = c->G;
     a.nseg = c->nseg;
+    a.gld = c->gld;
     a.grid = c->num_sms;
     a.smem = c->smem;
     return a;

@@ -166,11 +166,20 @@ int rebuild(tsp_batch* b, cudaStream_t st)
     std::vector<std::vector<int4>> lists(k);
     std::vector<int4> outl;
     for (int i = 0; i < k; ++i) {
-        lists[i] = tile_items(b->inst[i], E, i);
         const tsp_ctx* c = b->inst[i];
-        for (long long j = 0; j < c->n_outliers; j += 64)
-            outl.push_back(make_int4(-1, (int)(c->outlier_first + j),
-                                     (int)std::min<long long>(64, c->n_outliers - j), i));
+        // a reconstruction whose tiles stage only the accumulator is not
+        // supported by the batched tile kernel: all its events take the
+        // batched global-memory path
+        long long first = c->outlier_first, count = c->n_outliers;
+        if (c->gld) {
+            first = 0;
+            count = c->outlier_first + c->n_outliers;
+        } else {
+            lists[i] = tile_items(c, E, i);
+        }
+        for (long long j = 0; j < count; j += 64)
+            outl.push_back(make_int4(-1, (int)(first + j), (int)std::min<long long>(64, count - j),
+                                     i));
     }
     std::vector<int4> items;
     if (b->sched.order == 0) {

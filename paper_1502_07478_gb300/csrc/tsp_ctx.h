@@ -28,6 +28,7 @@ struct tsp_ctx {
     tsp::Geo g{};
     tsp::Tiling tl{};
     int lmax = 0, nseg = 1, G = 1;
+    int gld = 0;             // tiles stage only A, rho' read from global memory
     int need = 0;            // longest chord of a window row, in pixels (+2)
     int maxrows = 0;         // most rows of one window
     int dev = 0, num_sms = 0;

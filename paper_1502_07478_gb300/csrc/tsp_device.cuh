@@ -86,6 +86,12 @@ __host__ __device__ constexpr size_t tiles_smem_floats(int RH, int RS)
            6 * kWarps;
 }
 
+// The same with only the accumulator staged (rho' read from global memory).
+__host__ __device__ constexpr size_t tiles_acc_smem_floats(int RH, int RS)
+{
+    return (size_t)kPadFloats + (size_t)RH * RS + kPadFloats + 6 * kWarps;
+}
+
 // Device-side accumulators of one pass.
 struct Accum {
     unsigned long long n_used;   // events with D > 0

@@ -22,6 +22,7 @@ struct PassArgs {
     float* A;
     Accum* accum;
     int G, nseg;
+    int gld;           // tiles stage only A; rho' read from global (nseg = 2)
     int grid;          // persistent blocks
     size_t smem;       // dynamic shared memory of the tile kernel
 };

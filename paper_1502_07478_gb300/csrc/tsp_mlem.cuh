@@ -67,6 +67,7 @@ template <bool SMEM>
 struct RowK {
     int lim_odd, lim_even;
     typename std::conditional<SMEM, unsigned, unsigned long long>::type base;
+    unsigned long long gbase;   // rho' in global memory (tiles that stage only A)
     float Q0, dQ, A0, dA, su0, dsu, C0;
 };
 
@@ -111,11 +112,11 @@ __device__ __forceinline__ void row_idle(RowK<SMEM>& r, RowG& rg)
 // The event preparation guarantees that every chord lies inside the frame;
 // the clamp keeps every access in bounds regardless (clipped pixels are
 // counted).
-template <int TRAV, int LMAX, bool GRAD, bool SMEM>
+template <int TRAV, int LMAX, bool GRAD, bool SMEM, bool GLD>
 __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const Ev64* ev64,
                                          int iy, bool valid_row, const Frame* fp,
-                                         const float* base, RowK<SMEM>& r, RowG& rg,
-                                         BlockSums* bs)
+                                         const float* base, const float* gimg, RowK<SMEM>& r,
+                                         RowG& rg, BlockSums* bs)
 {
     row_idle<GRAD, SMEM>(r, rg);
     Chord c;
@@ -201,6 +202,7 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const E
         r.base = (unsigned)__cvta_generic_to_shared(base) + 4u * (unsigned)sidx;
     else
         r.base = (unsigned long long)(base + sidx);
+    if constexpr (GLD) r.gbase = (unsigned long long)(gimg + (size_t)iy * g.nz + o);
     r.Q0 = fmaf(gam2, u0, Qc);
     r.dQ = gam2 * g.dz;
     r.A0 = g.kA * fmaf(alpha, u0, beta);
@@ -260,6 +262,23 @@ __device__ __forceinline__ float load_acc(const RowK<SMEM>& r, int lim, int m, f
     return v;
 }
 
+// As load_acc, from global memory through the read-only path.
+template <int OFF>
+__device__ __forceinline__ float load_acc_g(unsigned long long base, int lim, int m, float p,
+                                            float& D)
+{
+    float v;
+    asm(
+        "{\n\t.reg .pred q;\n\t"
+        "setp.lt.s32 q, %2, %3;\n\t"
+        "mov.b32 %0, 0;\n\t"
+        "@q ld.global.nc.f32 %0, [%4+%5];\n\t"
+        "@q fma.rn.f32 %1, %6, %0, %1;\n\t}"
+        : "=&f"(v), "+f"(D)
+        : "r"(m), "r"(lim), "l"(base), "n"(OFF), "f"(p));
+    return v;
+}
+
 // Predicated reduction: if (m < len) mem[base + OFF] += v.
 template <bool SMEM, int OFF>
 __device__ __forceinline__ void red_add(const RowK<SMEM>& r, int lim, int m, float v)
@@ -285,7 +304,7 @@ __device__ __forceinline__ void red_add(const RowK<SMEM>& r, int lim, int m, flo
 // compile-time immediate).  P[M] holds the kernel value for M < len (values
 // beyond len are unspecified); Dp the partial denominator; in GRAD mode Ez, El
 // the partial sums of rho' P dlogP/d(iz) and rho' P dlogP/d(il).
-template <int TRAV, int LMAX, bool GRAD, bool SMEM, int M>
+template <int TRAV, int LMAX, bool GRAD, bool SMEM, bool GLD, int M>
 __device__ __forceinline__ void pass1_step(const RowK<SMEM>& r, const RowG& rg, int maxlen,
                                            float (&P)[LMAX], float& Dp, float& Ez, float& El)
 {
@@ -304,7 +323,11 @@ __device__ __forceinline__ void pass1_step(const RowK<SMEM>& r, const RowG& rg, 
         const float p = rq * ex2_approx(arg);
         P[M] = p;
         const int lim = (M & 1) ? r.lim_odd : r.lim_even;
-        const float rhop = load_acc<SMEM, 4 * d>(r, lim, M, p, Dp);
+        float rhop;
+        if constexpr (GLD)
+            rhop = load_acc_g<4 * d>(r.gbase, lim, M, p, Dp);
+        else
+            rhop = load_acc<SMEM, 4 * d>(r, lim, M, p, Dp);
         if constexpr (GRAD) {
             // d log P / d iz = 1/iz - u^2 + X Cz - (Qz/2)(1/Q + X^2)
             // d log P / d il = 1/(2 il) - Bl/2 + X Cl - (Ql/2)(1/Q + X^2)
@@ -324,7 +347,7 @@ __device__ __forceinline__ void pass1_step(const RowK<SMEM>& r, const RowG& rg, 
                 El = fmaf(wgt, dl_, El);
             }
         }
-        pass1_step<TRAV, LMAX, GRAD, SMEM, M + 1>(r, rg, maxlen, P, Dp, Ez, El);
+        pass1_step<TRAV, LMAX, GRAD, SMEM, GLD, M + 1>(r, rg, maxlen, P, Dp, Ez, El);
     }
 }
 
@@ -346,7 +369,9 @@ __device__ __forceinline__ void pass2_step(const RowK<SMEM>& r, int maxlen, cons
 // One event processed by a group of G warps; the lane holds row rows.x + rowi
 // with traversal TRAV.  part: 6*G floats of shared scratch for the group's
 // cross-warp reduction (double-buffered by parity).
-template <int TRAV, int LMAX, int MODE, bool SMEM>
+// GLD (tiles that stage only A): rho' is read from the global image rp_base
+// and the frame addresses the staged accumulator acc_base.
+template <int TRAV, int LMAX, int MODE, bool SMEM, bool GLD>
 __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, int e, int rowi,
                                            const Frame* f, const float* rp_base, float* acc_base,
                                            int G, int wig, int lane, int bar_id, float* part,
@@ -357,12 +382,12 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
     const int2 rws = evs.rows[e];
     RowK<SMEM> r;
     RowG rg;
-    make_row<TRAV, LMAX, GRAD, SMEM>(g, ev, evs.geo64 + e, rws.x + rowi, rowi < rws.y, f, rp_base,
-                                     r, rg, bs);
+    make_row<TRAV, LMAX, GRAD, SMEM, GLD>(g, ev, evs.geo64 + e, rws.x + rowi, rowi < rws.y, f,
+                                          GLD ? acc_base : rp_base, rp_base, r, rg, bs);
     const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(r.lim_odd, r.lim_even));
     float P[LMAX];
     float Dp = 0.0f, Ez = 0.0f, El = 0.0f;
-    pass1_step<TRAV, LMAX, GRAD, SMEM, 0>(r, rg, maxlen, P, Dp, Ez, El);
+    pass1_step<TRAV, LMAX, GRAD, SMEM, GLD, 0>(r, rg, maxlen, P, Dp, Ez, El);
     float D = warp_sum(Dp);
     if (GRAD) {
         Ez = warp_sum(Ez);
@@ -401,8 +426,10 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
         }
         if (MODE != kLoglik) {
             // the accumulator has the rho' buffer's layout at a fixed byte offset
+            // (GLD: the frame already addresses the accumulator)
             RowK<SMEM> ra = r;
-            ra.base += (decltype(ra.base))((const char*)acc_base - (const char*)rp_base);
+            if (!GLD)
+                ra.base += (decltype(ra.base))((const char*)acc_base - (const char*)rp_base);
             pass2_step<TRAV, LMAX, SMEM, 0>(ra, maxlen, P, 1.0f / D);
         }
     }
@@ -411,22 +438,24 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
 // NSEG = 1: lane-row q = wig*32 + lane covers its row whole (kAlt).  NSEG = 2:
 // even warps cover the right halves and odd warps the left halves of rows
 // (wig/2)*32 + lane (a warp-uniform choice, no divergence).
-template <int LMAX, int MODE, int NSEG, bool SMEM>
+template <int LMAX, int MODE, int NSEG, bool SMEM, bool GLD = false>
 __device__ __forceinline__ void process_event(const Geo& g, const EventsView& evs, int e, int G,
                                               int wig, int lane, int bar_id, float* part,
                                               int& parity, const Frame* f, const float* rp_base,
                                               float* acc_base, BlockSums* bs)
 {
     if constexpr (NSEG == 1) {
-        event_rows<kAlt, LMAX, MODE, SMEM>(g, evs, e, wig * 32 + lane, f, rp_base, acc_base, G,
-                                          wig, lane, bar_id, part, parity, bs);
+        event_rows<kAlt, LMAX, MODE, SMEM, GLD>(g, evs, e, wig * 32 + lane, f, rp_base, acc_base,
+                                               G, wig, lane, bar_id, part, parity, bs);
     } else {
         if ((wig & 1) == 0)
-            event_rows<kPos, LMAX, MODE, SMEM>(g, evs, e, (wig >> 1) * 32 + lane, f, rp_base,
-                                              acc_base, G, wig, lane, bar_id, part, parity, bs);
+            event_rows<kPos, LMAX, MODE, SMEM, GLD>(g, evs, e, (wig >> 1) * 32 + lane, f,
+                                                   rp_base, acc_base, G, wig, lane, bar_id, part,
+                                                   parity, bs);
         else
-            event_rows<kNeg, LMAX, MODE, SMEM>(g, evs, e, (wig >> 1) * 32 + lane, f, rp_base,
-                                              acc_base, G, wig, lane, bar_id, part, parity, bs);
+            event_rows<kNeg, LMAX, MODE, SMEM, GLD>(g, evs, e, (wig >> 1) * 32 + lane, f,
+                                                   rp_base, acc_base, G, wig, lane, bar_id, part,
+                                                   parity, bs);
     }
 }
 
@@ -484,7 +513,9 @@ __device__ __forceinline__ Frame tile_frame(const Geo& g, const Tiling& tl, int 
 // reconstruction).  Plain form (BATCH = false): one reconstruction, passed as
 // `p`.  Batched form: item.w indexes `table`, whose record is copied to shared
 // memory when it changes.  `queue` is the work counter (zero at launch).
-template <int LMAX, int MODE, int NSEG, bool BATCH>
+// GLD: only the accumulator is staged (windows too large for both regions);
+// rho' is read from the global image through the read-only cache.
+template <int LMAX, int MODE, int NSEG, bool BATCH, bool GLD = false>
 __global__ void __launch_bounds__(kThreads, 1)
 k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, int n_items,
         int* queue)
@@ -502,7 +533,7 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
     if (!BATCH) {
         const int region = p.tl.RH * p.tl.RS;
         float* s_rp = smem + kPadFloats;
-        float* s_acc = s_rp + region + 2 * kPadFloats;
+        float* s_acc = GLD ? s_rp : s_rp + region + 2 * kPadFloats;
         for (int k = tid; k < kPadFloats; k += kThreads) {
             s_rp[-kPadFloats + k] = 0.0f;
             s_rp[region + k] = 0.0f;
@@ -546,29 +577,35 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
         const int grp = warp / G, wig = warp - grp * G;
         const int region = tl.RH * tl.RS;
         float* s_rp = smem + kPadFloats;
-        float* s_acc = s_rp + region + 2 * kPadFloats;
+        float* s_acc = GLD ? s_rp : s_rp + region + 2 * kPadFloats;
         float* part = s_acc + region + kPadFloats + grp * (2 * 3 * G);
         int parity = 0;
         const Frame f = tile_frame(g, tl, item.x);
         if (tid == 0) s_frame = f;
-        for (int rr = warp; rr < tl.RH; rr += kWarps) {
-            const int iy = f.oy + rr;
-            const bool row_in = iy >= 0 && iy < g.ny;
-            const int z0row = f.zbase + (int)rintf(__fmul_rn(f.shear, (float)(iy - f.Y0)));
-            for (int cc = lane; cc < tl.RS; cc += 32) {
-                const int iz = z0row + cc;
-                float v = 0.0f;
-                if (row_in && cc < tl.RW && iz >= 0 && iz < g.nz)
-                    v = I.rhop[(size_t)iy * g.nz + iz];
-                s_rp[rr * tl.RS + cc] = v;
-                if (MODE != kLoglik) s_acc[rr * tl.RS + cc] = 0.0f;
+        if (GLD) {
+            if (MODE != kLoglik)
+                for (int k = tid; k < region; k += kThreads) s_acc[k] = 0.0f;
+        } else {
+            for (int rr = warp; rr < tl.RH; rr += kWarps) {
+                const int iy = f.oy + rr;
+                const bool row_in = iy >= 0 && iy < g.ny;
+                const int z0row = f.zbase + (int)rintf(__fmul_rn(f.shear, (float)(iy - f.Y0)));
+                for (int cc = lane; cc < tl.RS; cc += 32) {
+                    const int iz = z0row + cc;
+                    float v = 0.0f;
+                    if (row_in && cc < tl.RW && iz >= 0 && iz < g.nz)
+                        v = I.rhop[(size_t)iy * g.nz + iz];
+                    s_rp[rr * tl.RS + cc] = v;
+                    if (MODE != kLoglik) s_acc[rr * tl.RS + cc] = 0.0f;
+                }
             }
         }
         __syncthreads();
         if (grp < ngroups)
             for (int e = item.y + grp; e < item.y + item.z; e += ngroups)
-                process_event<LMAX, MODE, NSEG, true>(g, I.evs, e, G, wig, lane, 1 + grp, part,
-                                                      parity, &s_frame, s_rp, s_acc, &s_sums);
+                process_event<LMAX, MODE, NSEG, true, GLD>(g, I.evs, e, G, wig, lane, 1 + grp,
+                                                           part, parity, &s_frame,
+                                                           GLD ? I.rhop : s_rp, s_acc, &s_sums);
         __syncthreads();
         if (MODE != kLoglik) {
             for (int rr = warp; rr < tl.RH; rr += kWarps) {

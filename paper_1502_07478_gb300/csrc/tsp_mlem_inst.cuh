@@ -12,7 +12,7 @@ namespace tsp {
 
 namespace {
 
-template <int LMAX, int MODE, int NSEG>
+template <int LMAX, int MODE, int NSEG, bool GLD = false>
 cudaError_t run_pass(const PassArgs& a, cudaStream_t st)
 {
     if (a.n_items > 0) {
@@ -25,7 +25,7 @@ cudaError_t run_pass(const PassArgs& a, cudaStream_t st)
         p.accum = a.accum;
         p.G = a.G;
         p.pad = 0;
-        k_tiles<LMAX, MODE, NSEG, false><<<a.grid, kThreads, a.smem, st>>>(
+        k_tiles<LMAX, MODE, NSEG, false, GLD><<<a.grid, kThreads, a.smem, st>>>(
             p, nullptr, a.items, a.n_items, &a.accum->queue);
     }
     if (a.outlier_count > 0) {
@@ -41,8 +41,12 @@ cudaError_t run_pass(const PassArgs& a, cudaStream_t st)
 template <int LMAX, int MODE, int NSEG>
 cudaError_t set_smem(size_t smem)
 {
-    return cudaFuncSetAttribute(k_tiles<LMAX, MODE, NSEG, false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_tiles<LMAX, MODE, NSEG, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && NSEG == 2)
+        e = cudaFuncSetAttribute(k_tiles<LMAX, MODE, NSEG, false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e;
 }
 
 // Batched form: one persistent launch over the items of every reconstruction
@@ -85,6 +89,14 @@ cudaError_t batch_smem(size_t smem)
 template <int LMAX, int NSEG>
 cudaError_t run_mode(int mode, const PassArgs& a, cudaStream_t st)
 {
+    if (NSEG == 2 && a.gld) {
+        switch (mode) {
+        case kMlem: return run_pass<LMAX, kMlem, 2, true>(a, st);
+        case kLoglik: return run_pass<LMAX, kLoglik, 2, true>(a, st);
+        case kGrad: return run_pass<LMAX, kGrad, 2, true>(a, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (mode) {
     case kMlem: return run_pass<LMAX, kMlem, NSEG>(a, st);
     case kLoglik: return run_pass<LMAX, kLoglik, NSEG>(a, st);

@@ -219,6 +219,7 @@ extern "C" int tsp_mlem_update_noalloc(const tsp_params* params, const float* zu
     a.accum = accum;
     a.G = G;
     a.nseg = nseg;
+    a.gld = 0;
     a.grid = sms > 0 ? sms : 1;
     a.smem = 0;
     for (long long c0 = 0; c0 < n; c0 += TSP_NOALLOC_CHUNK) {

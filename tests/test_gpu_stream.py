@@ -2,9 +2,10 @@
 
 A streamed upload (tsp_begin_events / tsp_append_events / tsp_end_events) must
 give the reconstruction of a single upload of the concatenated chunks, from
-host arrays, pinned host tensors or device tensors.  The 0.5 mm grid of the
-stress workload has windows too large for a staged tile; its events take the
-global-memory path and must still match the FP64 oracle.
+host arrays, pinned host tensors or device tensors.  On the 0.5 mm grid of the
+stress workload the window halo is too large to stage both rho' and the
+accumulator; the tiles stage only the accumulator, read rho' from global
+memory and split each row over two lanes, and must still match the FP64 oracle.
 """
 import numpy as np
 import pytest
@@ -98,8 +99,8 @@ def test_streamed_upload_state_errors(prob):
     r.close()
 
 
-def test_fine_grid_global_path_matches_oracle():
-    """0.5 mm pixels (1400 x 1000): every event takes the global-memory path."""
+def test_fine_grid_accumulator_tiles_match_oracle():
+    """0.5 mm pixels (1400 x 1000): accumulator-only tiles."""
     w = make_workload("stress_05mm", n_events=3000)
     ev = w.events()
     from paper_1502_07478_gb300 import Recon
@@ -109,7 +110,7 @@ def test_fine_grid_global_path_matches_oracle():
     img = r.read_image().cpu().numpy()
     st = r.stats()
     r.close()
-    assert st["n_outliers"] == st["n_events"] - st["n_empty"]
+    assert st["n_outliers"] < 0.05 * st["n_events"]
     assert st["n_clipped"] == 0 and st["n_qbad"] == 0
     ref, rst = oracle.mlem(Setup.from_workload(w), ev, 3)
     assert st["n_used"] == rst.n_used
