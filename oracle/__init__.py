@@ -92,6 +92,7 @@ def lib():
         _lib.orc_update_at_pixels.restype = C.c_int
         _lib.orc_loglik_grad.argtypes = [P(Params), dp, dp, dp, C.c_int64, dp, dp, dp, dp, dp]
         _lib.orc_loglik_grad.restype = C.c_int
+        _lib.orc_direct_image.argtypes = [P(Params), dp, dp, dp, C.c_int64, dp]
     return _lib
 
 
@@ -247,6 +248,15 @@ def denominators(st: Setup, events, rho, s=None):
     lib().orc_denominators(C.byref(p), _dp(zu), _dp(zd), _dp(dl), n, _dp(s), _dp(rho), _dp(D),
                            cnt.ctypes.data_as(C.POINTER(C.c_int64)))
     return D, cnt
+
+
+def direct_image(st: Setup, events) -> np.ndarray:
+    """Counts of the events' direct reconstructions (Eq. 2) per pixel, (ny, nz)."""
+    zu, zd, dl = (_f64(e) for e in events)
+    out = np.zeros(st.ny * st.nz)
+    p = st.params()
+    lib().orc_direct_image(C.byref(p), _dp(zu), _dp(zd), _dp(dl), zu.size, _dp(out))
+    return out.reshape(st.ny, st.nz)
 
 
 def update_at_pixels(st: Setup, events, rho, pixels, s=None):

@@ -451,6 +451,24 @@ int orc_denominators(const orc_params* p, const double* zu, const double* zd,
 /* One MLEM update evaluated only at the listed pixels: out[k] = rho^(t+1) at
  * pixel pix[k], from Eq. iter with the current rho.  Events whose window misses
  * every listed pixel are skipped before their denominator is formed. */
+/* Direct-reconstruction image (Eq. 2, Sec. 2; the paper's direct image): the
+ * number of events whose reconstructed point (y~, z~) falls in each pixel.
+ * Pixel (iy, iz) covers y in [-R + iy dy, -R + (iy+1) dy) and z in
+ * [-L/2 + iz dz, -L/2 + (iz+1) dz); points outside the grid are not counted.
+ * counts: ny*nz doubles, accumulated (the caller zeroes them). */
+void orc_direct_image(const orc_params* p, const double* zu, const double* zd,
+                      const double* dl, int64_t n, double* counts)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        double y, z, t;
+        orc_direct(p, zu[j], zd[j], dl[j], &y, &z, &t);
+        double fy = (y + p->R) / p->dy, fz = (z + 0.5 * p->L) / p->dz;
+        if (!(fy >= 0.0 && fy < (double)p->ny && fz >= 0.0 && fz < (double)p->nz)) continue;
+        int iy = (int)floor(fy), iz = (int)floor(fz);
+        counts[(int64_t)iy * p->nz + iz] += 1.0;
+    }
+}
+
 int orc_update_at_pixels(const orc_params* p, const double* zu, const double* zd,
                          const double* dl, int64_t n, const double* s, const double* rho,
                          const int64_t* pix, int32_t npx, double* out)

@@ -63,3 +63,26 @@ def test_printed_second_forms_do_not_invert():
     ey, ez, _ = oracle.direct(ST, zu, zd, dl)
     assert (ey, ez) == pytest.approx((y, z), abs=1e-9)
     assert abs(y_printed - y) > 100.0 and abs(z_printed - z) > 10.0
+
+
+def test_direct_image_is_the_histogram_of_the_emission_points():
+    """The direct image of noise-free events is the 2-D histogram of their
+    emission points (points kept at least a quarter pixel from pixel edges, so
+    that the exact inversion decides every bin), and points beyond the grid
+    (|y| > R is impossible; |z| > L/2 here) are not counted."""
+    rng = np.random.default_rng(21)
+    n = 20000
+    iy = rng.integers(0, ST.ny, n)
+    iz = rng.integers(-3, ST.nz + 3, n)          # some columns beyond the grid
+    fy = rng.uniform(0.25, 0.75, n)
+    fz = rng.uniform(0.25, 0.75, n)
+    y = -ST.R + (iy + fy) * ST.dy
+    z = -0.5 * ST.L + (iz + fz) * ST.dz
+    th = rng.uniform(-0.6, 0.6, n)
+    zu, zd, dl = _trace(y, z, th, ST.R)
+    img = oracle.direct_image(ST, (zu, zd, dl))
+    inside = (iz >= 0) & (iz < ST.nz)
+    ref = np.zeros((ST.ny, ST.nz))
+    np.add.at(ref, (iy[inside], iz[inside]), 1.0)
+    np.testing.assert_array_equal(img, ref)
+    assert img.sum() == inside.sum() < n
