@@ -135,6 +135,13 @@ int tsp_set_image(tsp_ctx* ctx, const float* rho, int on_device, void* stream);
  * (TSP_ESTATE otherwise).  Asynchronous on stream. */
 int tsp_iterate(tsp_ctx* ctx, int n_iter, void* stream);
 
+/* Direct-reconstruction image (Eq. 2, Sec. 2): out[iy*nz + iz] = the number of
+ * uploaded events whose point (y~, z~) lies in pixel (iy, iz), i.e. y~ in
+ * [-R + iy dy, -R + (iy+1) dy) and z~ in [-L/2 + iz dz, -L/2 + (iz+1) dz)
+ * (ny*nz floats, host or device; events outside the grid are not counted).
+ * Eq. 2 is evaluated in double precision.  Requires an upload (TSP_ESTATE). */
+int tsp_direct_image(tsp_ctx* ctx, float* out, int on_device, void* stream);
+
 /* Copy the current image to out (ny*nz floats, host or device).  which = 0:
  * rho of Eq. iter; which = 1: rho' = s * rho of Eq. iter-p. */
 int tsp_read_image(tsp_ctx* ctx, float* out, int which, int on_device, void* stream);

@@ -62,6 +62,7 @@ SIGNATURES = [
     ("tsp_set_image", C.c_int, [_vp, _fp, C.c_int, _vp]),
     ("tsp_iterate", C.c_int, [_vp, C.c_int, _vp]),
     ("tsp_read_image", C.c_int, [_vp, _fp, C.c_int, C.c_int, _vp]),
+    ("tsp_direct_image", C.c_int, [_vp, _fp, C.c_int, _vp]),
     ("tsp_loglik", C.c_int, [_vp, C.POINTER(C.c_double), _vp]),
     ("tsp_loglik_grad", C.c_int, [_vp, C.POINTER(C.c_double), _fp, C.c_int,
                                   C.POINTER(C.c_double), _vp]),

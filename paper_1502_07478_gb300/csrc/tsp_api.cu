@@ -95,6 +95,7 @@ int plan(tsp_ctx* c)
     g.izd = iz;
     g.ild = il;
     g.cut2d = cut * cut;
+    g.Ld = p.L;
 
     // lane capacity: the longest chord of the ellipse is 2 cut sigma_z / sqrt(2)
     const double umax = cut * p.sigma_z / std::sqrt(2.0);
@@ -775,6 +776,29 @@ int tsp_set_profiling(tsp_ctx* c, int on)
         TSP_CUDA(c, cudaDeviceSynchronize());
         clear_graphs(c);
         c->profiling = on != 0;
+    }
+    return TSP_OK;
+}
+
+int tsp_direct_image(tsp_ctx* c, float* out, int on_device, void* stream)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (!out) return fail(c, TSP_EINVAL, "out is NULL");
+    if (!c->uploaded) return fail(c, TSP_ESTATE, "direct_image before upload_events");
+    DeviceGuard dg(c->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    // integer counts in the gradient buffer (reinterpreted); the float image
+    // goes to out, or for a host destination to A (all zero between passes),
+    // which is copied out and cleared again
+    float* dst = on_device ? out : c->A;
+    TSP_CUDA(c, launch_direct_image(c->g, c->n, c->zu, c->zd, c->dl,
+                                    reinterpret_cast<unsigned*>(c->gbuf), dst, st));
+    c->launches += 2;
+    if (!on_device) {
+        int rc = copy_floats(c, out, c->A, c->npix, 0, 1, st);
+        if (rc) return rc;
+        TSP_CUDA(c, cudaMemsetAsync(c->A, 0, sizeof(float) * c->npix, st));
+        TSP_CUDA(c, cudaStreamSynchronize(st));
     }
     return TSP_OK;
 }

@@ -42,6 +42,7 @@ struct Geo {
     float inv_sqrt_2iz;     // 1 / sqrt(2 iz)
     // double-precision copies for the exact window decision near its boundary
     double y0d, z0d, dyd, dzd, Rd, izd, ild, cut2d;
+    double Ld;              // strip length
 };
 
 // Image tiling used by the shared-memory accumulation.

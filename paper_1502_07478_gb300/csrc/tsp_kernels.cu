@@ -306,6 +306,37 @@ __global__ void k_batch_pixels(const BatchImg* __restrict__ im, int op)
     if (threadIdx.x == 0) atomicAdd(&b.accum->sum_rhop, acc);
 }
 
+// Direct-reconstruction image (Eq. 2, Sec. 2): count the events whose point
+// (y~, z~) falls in each pixel.  Evaluated in double precision with every
+// operation explicitly rounded (no contraction), in the order of Eq. 2's first
+// forms: t = (zu - zd) / 2R, y~ = -dl / 2 / sqrt(1 + t^2),
+// z~ = (zu + zd + 2 y~ t) / 2; pixel (iy, iz) covers [-R + iy dy, +dy) x
+// [-L/2 + iz dz, +dz).
+__global__ void k_direct_hist(Geo g, long long n, const float* __restrict__ zu,
+                              const float* __restrict__ zd, const float* __restrict__ dl,
+                              unsigned* __restrict__ h)
+{
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        const double u = zu[j], d = zd[j], l = dl[j];
+        if (!(isfinite(u) && isfinite(d) && isfinite(l))) continue;
+        const double t = __ddiv_rn(__dsub_rn(u, d), __dmul_rn(2.0, g.Rd));
+        const double y = __ddiv_rn(__dmul_rn(-0.5, l), __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(t, t))));
+        const double z =
+            __dmul_rn(0.5, __dadd_rn(__dadd_rn(u, d), __dmul_rn(__dmul_rn(2.0, y), t)));
+        const double fy = __ddiv_rn(__dadd_rn(y, g.Rd), g.dyd);
+        const double fz = __ddiv_rn(__dadd_rn(z, __dmul_rn(0.5, g.Ld)), g.dzd);
+        if (!(fy >= 0.0 && fy < (double)g.ny && fz >= 0.0 && fz < (double)g.nz)) continue;
+        atomicAdd(&h[(size_t)(int)floor(fy) * g.nz + (int)floor(fz)], 1u);
+    }
+}
+
+__global__ void k_counts_to_float(int n, const unsigned* __restrict__ h, float* __restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = (float)h[i];
+}
+
 __global__ void k_fill(float* p, long long n, float v)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -395,6 +426,20 @@ cudaError_t launch_set_rhop(int npix, const float* rho, const float* s, float* r
 {
     k_set_rhop<<<blocks_for(npix, kAuxThreads * 4, 1024), kAuxThreads, 0, st>>>(npix, rho, s, rhop,
                                                                                accum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_direct_image(const Geo& g, long long n, const float* zu, const float* zd,
+                                const float* dl, unsigned* h, float* out, cudaStream_t st)
+{
+    const int npix = g.ny * g.nz;
+    cudaError_t e = cudaMemsetAsync(h, 0, sizeof(unsigned) * (size_t)npix, st);
+    if (e != cudaSuccess) return e;
+    if (n > 0)
+        k_direct_hist<<<blocks_for(n, kAuxThreads * 8, 4096), kAuxThreads, 0, st>>>(g, n, zu, zd,
+                                                                                  dl, h);
+    k_counts_to_float<<<blocks_for(npix, kAuxThreads * 4, 1024), kAuxThreads, 0, st>>>(npix, h,
+                                                                                      out);
     return cudaGetLastError();
 }
 

@@ -93,6 +93,8 @@ cudaError_t launch_set_rhop(int npix, const float* rho, const float* s, float* r
                             cudaStream_t st);
 cudaError_t launch_batch_begin(const BatchImg* im, int k, int* queue, cudaStream_t st);
 cudaError_t launch_batch_pixels(const BatchImg* im, int k, int max_npix, int op, cudaStream_t st);
+cudaError_t launch_direct_image(const Geo& g, long long n, const float* zu, const float* zd,
+                                const float* dl, unsigned* h, float* out, cudaStream_t st);
 cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t st);
 cudaError_t launch_product(int npix, const float* a, const float* b, float* out, cudaStream_t st);
 cudaError_t launch_check_image(int npix, const float* rho, int* bad, cudaStream_t st);

@@ -135,6 +135,7 @@ int geometry(const tsp_params& p, Geo& g, int& lmax, int& nseg, int& G, char* er
     g.izd = iz;
     g.ild = il;
     g.cut2d = cut * cut;
+    g.Ld = p.L;
     const int need = (int)std::floor(2.0 * cut * p.sigma_z / std::sqrt(2.0) / dz) + 2;
     lmax = 0;
     for (int k = 0; k < kLmaxCount && !lmax; ++k)

@@ -162,6 +162,23 @@ class Recon:
         self._chk(self._lib.tsp_read_image(self._h, p, int(which), dev, _stream_handle(stream)))
         return out
 
+    def direct_image(self, out=None, stream=None):
+        """Counts of the events' direct reconstructions (Eq. 2) per pixel, as a
+        CUDA tensor or into ``out`` (CUDA tensor or NumPy array)."""
+        if out is None:
+            out = torch.empty(self.ny, self.nz, dtype=torch.float32, device="cuda")
+        if isinstance(out, np.ndarray):
+            if out.dtype != np.float32 or not out.flags.c_contiguous or out.size != self.ny * self.nz:
+                raise ValueError("out must be a contiguous float32 array of ny*nz elements")
+            self._chk(self._lib.tsp_direct_image(self._h, C.c_void_p(out.ctypes.data), 0,
+                                                 _stream_handle(stream)))
+            return out
+        p, dev, keep = _arg(out)
+        if keep is not out:
+            raise ValueError("out must be a contiguous float32 CUDA tensor")
+        self._chk(self._lib.tsp_direct_image(self._h, p, dev, _stream_handle(stream)))
+        return out
+
     def loglik(self, stream=None) -> float:
         v = C.c_double()
         self._chk(self._lib.tsp_loglik(self._h, C.byref(v), _stream_handle(stream)))

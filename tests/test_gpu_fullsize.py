@@ -123,6 +123,7 @@ def test_adjoint_full_gradient():
     Lref, gref, gsref = oracle.loglik_grad(Setup.from_workload(w, sigma_z=14.0, sigma_dl=55.0),
                                            ev, rho)
     g = g.cpu().numpy().astype(np.float64).ravel()
+    gref = np.asarray(gref).ravel()
     assert L == pytest.approx(Lref, rel=1e-6)
     assert np.linalg.norm(g - gref) / np.linalg.norm(gref) <= 1e-4
     np.testing.assert_allclose(gs, gsref, rtol=1e-3)
