@@ -436,6 +436,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-vs-plain comparison")
+    ap.add_argument("--variant", default="tiles", choices=["tiles", "thread"],
+                    help="MLEM pass: the tile kernel, or one thread per event (ablation)")
     args = ap.parse_args()
 
     from synth import make_workload
@@ -474,6 +476,7 @@ def main():
     # pinned host copies for the end-to-end leg
     pinned = [torch.from_numpy(e).pin_memory() for e in ev]
     r = Recon.from_workload(workload)
+    r.set_variant(args.variant)
     r.upload_events(*ev)
     r.set_profiling(True)
     stream = torch.cuda.current_stream()
@@ -531,9 +534,11 @@ def main():
                 "peak": peak / 1e9, "unit": "Gpixel-evals/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": (TILE_PASS_DRAM_B_PER_EVENT * n
-                            if workload.name == "paper_1mm" and workload.dz == 1.0 else None),
+                            if workload.name == "paper_1mm" and args.variant == "tiles"
+                            else None),
                 "traffic_basis": "ncu DRAM bytes of one 1e6-event launch, scaled by events",
-                "kernel": "k_tiles (MLEM pass, per launch)", "pixel_evals_per_launch": W,
+                "kernel": ("k_tiles" if args.variant == "tiles" else "k_thread_events") +
+                          " (MLEM pass, per launch)", "pixel_evals_per_launch": W,
                 "launch_ms": t_pass * 1e3,
                 "peak_basis": f"{sms} SMs x {f_max/1e6:.0f} MHz x {MUFU_PER_SM_CLK} SFU ops/clk"
                               f" / {MUFU_PER_PIXEL} SFU ops per pixel evaluation"}
@@ -588,6 +593,7 @@ def main():
                    "grid": [workload.ny, workload.nz], "pixel_mm": workload.dz,
                    "sigma_z": workload.sigma_z, "sigma_dl": workload.sigma_dl,
                    "cut": workload.cut, "form": "plain",
+                   "kernel_variant": args.variant,
                    "l2": "inputs larger than L2 (prepared events 24 B x 1e7 = 240 MB)",
                    "parallelism": f"{ws} independent reconstructions" if ws > 1 else "1 GPU"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,

@@ -198,6 +198,14 @@ typedef struct {
     int32_t reserved;
 } tsp_schedule;
 
+/* MLEM pass variant of tsp_iterate: 0 = the tile kernel (default); 1 = one
+ * thread per event (the thread-granularity kernel shape of Sec. 4.2, an
+ * ablation: the window is walked row by row by one thread, rho' read from
+ * global memory, P evaluated twice, the scatter done by global atomics).
+ * Both give the same images up to float rounding order.  Other values give
+ * TSP_EINVAL.  The log-likelihood and gradient passes always use the tiles. */
+int tsp_set_variant(tsp_ctx* ctx, int variant);
+
 /* Current schedule of ctx (default 128, 8, 0). */
 int tsp_get_schedule(tsp_ctx* ctx, tsp_schedule* out);
 /* Set the schedule; the uploaded events are re-binned (images are kept).

@@ -70,6 +70,7 @@ SIGNATURES = [
     ("tsp_stats", C.c_int, [_vp, C.POINTER(Stats), _vp]),
     ("tsp_set_profiling", C.c_int, [_vp, C.c_int]),
     ("tsp_pass_times", C.c_int, [_vp, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int), _vp]),
+    ("tsp_set_variant", C.c_int, [_vp, C.c_int]),
     ("tsp_get_schedule", C.c_int, [_vp, C.POINTER(Schedule)]),
     ("tsp_set_schedule", C.c_int, [_vp, C.POINTER(Schedule), _vp]),
     ("tsp_autotune", C.c_int, [_vp, C.POINTER(Schedule), C.POINTER(C.c_float), _vp]),

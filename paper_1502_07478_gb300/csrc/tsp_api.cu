@@ -44,6 +44,21 @@ long long pass_launches(const tsp_ctx* c)
     return (c->n_items > 0 ? 1 : 0) + (c->n_outliers > 0 ? 1 : 0);
 }
 
+// One MLEM pass of the context's variant.
+cudaError_t launch_mlem_pass(tsp_ctx* c, const PassArgs& a, cudaStream_t st)
+{
+    if (c->variant == 1)
+        return launch_thread_pass(c->g, a.evs, (int)(c->outlier_first + c->n_outliers), c->rhop,
+                                  c->A, c->accum, c->num_sms, st);
+    return launch_pass(c->lmax, kMlem, a, st);
+}
+
+long long mlem_pass_launches(const tsp_ctx* c)
+{
+    if (c->variant == 1) return c->outlier_first + c->n_outliers > 0 ? 1 : 0;
+    return pass_launches(c);
+}
+
 size_t dyn_smem_limit(int dev)
 {
     int optin = 0;
@@ -411,7 +426,7 @@ int capture_iterations(tsp_ctx* c, int n_iter, tsp_ctx::Graph* out)
         e = launch_begin(c->accum, cs);
         if (e == cudaSuccess && c->profiling)
             e = cudaEventRecordWithFlags(ev[2 * it], cs, cudaEventRecordExternal);
-        if (e == cudaSuccess) e = launch_pass(c->lmax, kMlem, a, cs);
+        if (e == cudaSuccess) e = launch_mlem_pass(c, a, cs);
         if (e == cudaSuccess && c->profiling)
             e = cudaEventRecordWithFlags(ev[2 * it + 1], cs, cudaEventRecordExternal);
         if (e == cudaSuccess) e = launch_finalize(c->npix, c->rho, c->rhop, c->A, c->s, c->accum, cs);
@@ -430,7 +445,7 @@ int capture_iterations(tsp_ctx* c, int n_iter, tsp_ctx::Graph* out)
         return fail(c, TSP_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
     out->exec = exec;
-    out->launches = (long long)n_iter * (2 + pass_launches(c));
+    out->launches = (long long)n_iter * (2 + mlem_pass_launches(c));
     out->ev = std::move(ev);
     return TSP_OK;
 }
@@ -799,6 +814,19 @@ int tsp_direct_image(tsp_ctx* c, float* out, int on_device, void* stream)
         if (rc) return rc;
         TSP_CUDA(c, cudaMemsetAsync(c->A, 0, sizeof(float) * c->npix, st));
         TSP_CUDA(c, cudaStreamSynchronize(st));
+    }
+    return TSP_OK;
+}
+
+int tsp_set_variant(tsp_ctx* c, int variant)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (variant != 0 && variant != 1) return fail(c, TSP_EINVAL, "variant must be 0 or 1");
+    if (variant != c->variant) {
+        DeviceGuard dg(c->dev);
+        TSP_CUDA(c, cudaDeviceSynchronize());
+        clear_graphs(c);
+        c->variant = variant;
     }
     return TSP_OK;
 }

@@ -29,6 +29,7 @@ struct tsp_ctx {
     tsp::Tiling tl{};
     int lmax = 0, nseg = 1, G = 1;
     int gld = 0;             // tiles stage only A, rho' read from global memory
+    int variant = 0;         // MLEM pass: 0 tiles, 1 one thread per event
     int need = 0;            // longest chord of a window row, in pixels (+2)
     int maxrows = 0;         // most rows of one window
     int dev = 0, num_sms = 0;

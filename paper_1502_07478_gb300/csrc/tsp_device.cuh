@@ -215,14 +215,16 @@ struct Chord {
 // when rem = cut2 - B0 is within its own error bound of 0, so that membership
 // agrees with a double-precision evaluation of bCb <= cut^2 at every pixel.
 // The bounds are a few times the worst-case error of the single-precision
-// expressions (below 2e-4 pixel on the workloads' grids):
+// expressions (below 4e-4 pixel on the workloads' grids), including the
+// relative error of the approximate reciprocal square root that gives
+// sqrt(rem) (2^-22.9 for rsqrt.approx):
 //   end:  kEndRel * (|x| + (|zc| + umax + |z0|)/dz)            (coordinates)
 //       + kEndRel * cut2 / sqrt(rem) / sqrt(2 iz) / dz           (from umax)
 //   rem:  kRemRel * cut2
 // The check evaluates bCb in double precision at the pixels next to the
 // uncertain end (the error is far below one pixel, so an end moves by at most
 // one column) -- only multiplications and additions, no division or root.
-constexpr float kEndRel = 5e-7f;
+constexpr float kEndRel = 1e-6f;
 constexpr float kRemRel = 1e-5f;
 
 // bCb of column iz in the row with offset Dy (B0 = 4 il Dy^2 c2i), double
@@ -256,13 +258,14 @@ __device__ __forceinline__ Chord row_chord(const Geo& g, const float4& ev,
     bool unsure_lo = false, unsure_hi = false;
     int a = 0, b = -1;                                // candidate columns [a, b]
     if (rem >= 0.0f) {
-        const float sr = __fsqrt_rn(rem);
+        const float rs = rsqrt_approx(fmaxf(rem, 1e-30f));   // 1/sqrt(rem)
+        const float sr = __fmul_rn(rem, rs);                  // sqrt(rem)
         const float umax = __fmul_rn(sr, g.inv_sqrt_2iz);
         const float xlo = __fmul_rn(__fsub_rn(__fsub_rn(c.zc, umax), g.z0), g.inv_dz);
         const float xhi = __fmul_rn(__fsub_rn(__fadd_rn(c.zc, umax), g.z0), g.inv_dz);
         const float coord = (fabsf(c.zc) + umax + fabsf(g.z0)) * g.inv_dz;
         const float m = kEndRel * (fabsf(xhi) + coord) +
-                        kEndRel * g.cut2 * g.inv_sqrt_2iz * g.inv_dz / fmaxf(sr, 1e-20f);
+                        kEndRel * g.cut2 * g.inv_sqrt_2iz * g.inv_dz * rs;
         unsure_lo = fabsf(xlo - rintf(xlo)) < m;
         unsure_hi = fabsf(xhi - rintf(xhi)) < m;
         a = float_to_index(ceilf(xlo));
@@ -301,6 +304,25 @@ __device__ __forceinline__ Chord row_chord(const Geo& g, const float4& ev,
         if (c.count == 0) c.lo = 0;
     }
     return c;
+}
+
+// Row polynomials of Eq. kernel along the chord of row c (u = z - zc):
+//   Q(u) = aCa + 2 oCb = Qc + gam2 u,    aCb(u) = alpha u + beta.
+__device__ __forceinline__ void row_q(const Geo& g, const float4& ev, const Chord& c, float& Qc,
+                                      float& gam2)
+{
+    const float t = ev.z, c2i = ev.w, y = c.y, Dy = c.Dy, y2 = y * y;
+    const float aCa = 2.0f * g.iz * (g.R * g.R + y2) * c2i * c2i + 4.0f * g.il * y2 * t * t * c2i;
+    Qc = aCa + 4.0f * g.il * y * fmaf(2.0f * t, t, 1.0f) * Dy * c2i;   // Q at u = 0
+    gam2 = -4.0f * g.iz * y * t * c2i;                                 // 2 oCb slope
+}
+
+__device__ __forceinline__ void row_acb(const Geo& g, const float4& ev, const Chord& c,
+                                        float& alpha, float& beta)
+{
+    const float t = ev.z, c2i = ev.w, y = c.y, Dy = c.Dy;
+    alpha = -2.0f * g.iz * y * c2i;            // aCb slope in u
+    beta = 4.0f * g.il * y * t * Dy * c2i;     // aCb at u = 0
 }
 
 // Bounding box of the event's window in pixel rows and columns, clipped to the

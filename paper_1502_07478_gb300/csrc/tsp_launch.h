@@ -93,6 +93,9 @@ cudaError_t launch_set_rhop(int npix, const float* rho, const float* s, float* r
                             cudaStream_t st);
 cudaError_t launch_batch_begin(const BatchImg* im, int k, int* queue, cudaStream_t st);
 cudaError_t launch_batch_pixels(const BatchImg* im, int k, int max_npix, int op, cudaStream_t st);
+// Thread-granularity MLEM pass over the n binned events (tsp_thread.cu).
+cudaError_t launch_thread_pass(const Geo& g, const EventsView& evs, int n, const float* rhop,
+                               float* A, Accum* accum, int sms, cudaStream_t st);
 cudaError_t launch_direct_image(const Geo& g, long long n, const float* zu, const float* zd,
                                 const float* dl, unsigned* h, float* out, cudaStream_t st);
 cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t st);

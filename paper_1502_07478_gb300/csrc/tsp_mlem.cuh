@@ -140,11 +140,7 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const E
             hi = hi2;
         }
         if (hi >= lo) {
-            const float t = ev.z, c2i = ev.w, y = c.y, Dy = c.Dy, y2 = y * y;
-            const float aCa =
-                2.0f * g.iz * (g.R * g.R + y2) * c2i * c2i + 4.0f * g.il * y2 * t * t * c2i;
-            Qc = aCa + 4.0f * g.il * y * fmaf(2.0f * t, t, 1.0f) * Dy * c2i;   // Q at u = 0
-            gam2 = -4.0f * g.iz * y * t * c2i;                                 // 2 oCb slope
+            row_q(g, ev, c, Qc, gam2);
             // Reading R5: P = 0 where Q <= 0.  Q is linear along the chord, so
             // the pixels with Q > 0 form a sub-range; keep only that.
             const float ulo = fmaf((float)lo, g.dz, g.z0) - c.zc;
@@ -194,8 +190,8 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const E
         r.lim_odd = r.lim_even = L;
     }
     const float t = ev.z, c2i = ev.w, y = c.y, Dy = c.Dy;
-    const float alpha = -2.0f * g.iz * y * c2i;                                    // aCb slope in u
-    const float beta = 4.0f * g.il * y * t * Dy * c2i;                             // aCb at u = 0
+    float alpha, beta;
+    row_acb(g, ev, c, alpha, beta);
     const float u0 = fmaf((float)o, g.dz, g.z0) - c.zc;
     const int sidx = (iy - f.oy) * f.stride + (o - z0row);
     if constexpr (SMEM)

@@ -208,6 +208,12 @@ class Recon:
     def set_profiling(self, on: bool = True):
         self._chk(self._lib.tsp_set_profiling(self._h, int(bool(on))))
 
+    def set_variant(self, variant: str = "tiles"):
+        """MLEM pass of iterate(): "tiles" (default) or "thread" (one thread per
+        event, the thread-granularity ablation)."""
+        code = {"tiles": 0, "thread": 1}[variant]
+        self._chk(self._lib.tsp_set_variant(self._h, code))
+
     @property
     def schedule(self) -> dict:
         s = L.Schedule()

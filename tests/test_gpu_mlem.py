@@ -232,3 +232,32 @@ def test_direct_image_paper_scale_exact():
     img = r.direct_image().cpu().numpy()
     r.close()
     np.testing.assert_array_equal(img, oracle.direct_image(Setup.from_workload(w), ev))
+
+
+def test_thread_granularity_variant_matches_oracle(small):
+    """The one-thread-per-event ablation gives the oracle's image."""
+    w, ev = small
+    r = _recon(w)
+    r.set_variant("thread")
+    r.upload_events(*ev)
+    r.iterate(5)
+    img = r.read_image(out=np.empty((w.ny, w.nz), np.float32))
+    st = r.stats()
+    r.close()
+    ref, rst = oracle.mlem(Setup.from_workload(w), ev, 5)
+    assert rel_err(img, ref) <= TOL
+    assert st["n_used"] == rst.n_used
+
+
+def test_thread_granularity_variant_matches_tiles_1mm():
+    w = make_workload("paper_1mm", n_events=20_000)
+    ev = w.events()
+    out = []
+    for v in ("tiles", "thread"):
+        r = _recon(w)
+        r.set_variant(v)
+        r.upload_events(*ev)
+        r.iterate(3)
+        out.append(r.read_image(out=np.empty((w.ny, w.nz), np.float32)))
+        r.close()
+    assert rel_err(out[1], out[0].astype(np.float64)) <= 1e-5
