@@ -20,8 +20,13 @@ def _setup(scale=1.0, **kw):
                  sigma_dl=42.0 * scale, **kw)
 
 
+def _cinv(st):
+    iz, il, g = st.sigma_z ** -2, st.sigma_dl ** -2, st.gamma
+    return np.array([[iz, 0.0, g], [0.0, iz, -g], [g, -g, il]])
+
+
 def _exact(st, ev, py, pz):
-    Ci = np.diag([st.sigma_z ** -2, st.sigma_z ** -2, st.sigma_dl ** -2])
+    Ci = _cinv(st)
     norm = np.sqrt(np.linalg.det(Ci)) / (2 * np.pi) ** 1.5 / np.pi
     R = st.R
     e_meas = np.asarray(ev)
@@ -167,3 +172,32 @@ def test_dlog_sigma_matches_finite_differences():
             fd = (np.log(oracle.kernel(sp, *args)[0]) - np.log(oracle.kernel(sm, *args)[0])) \
                 / (2 * h * getattr(st, name))
             assert g[k] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_kernel_with_gamma_matches_exact_quadrature():
+    """With the cross term gamma of C^-1 (Sec. 3) the Laplace kernel follows the
+    exact theta-integral of the correlated Gaussian as closely as the diagonal
+    kernel does, while differing from the diagonal kernel by far more (so the
+    gamma terms of aC^-1a, oC^-1b and aC^-1b are exercised)."""
+    st0 = _setup()
+    g = 0.5 * np.sqrt(st0.sigma_z ** -2 * st0.sigma_dl ** -2 / 2.0)   # det(C^-1) > 0
+    st = _setup(gamma=g)
+    rng = np.random.default_rng(41)
+    errs, shifts = [], []
+    while len(errs) < 60:
+        py = rng.uniform(-300.0, 300.0)
+        pz = rng.uniform(-200.0, 200.0)
+        th = rng.uniform(-0.6, 0.6)
+        ev = (pz + (st.R - py) * np.tan(th) + rng.normal() * st.sigma_z,
+              pz - (st.R + py) * np.tan(th) + rng.normal() * st.sigma_z,
+              -2.0 * py / np.cos(th) + rng.normal() * st.sigma_dl)
+        ey, ez, t = oracle.direct(st, *ev)
+        P, bq = oracle.kernel(st, ey, ez, t, py, pz)
+        if bq > st.cut ** 2:
+            continue
+        P0, _ = oracle.kernel(st0, ey, ez, t, py, pz)
+        errs.append(abs(P / _exact(st, ev, py, pz) - 1.0))
+        shifts.append(abs(P / P0 - 1.0))
+    errs, shifts = np.array(errs), np.array(shifts)
+    assert errs.mean() < 0.01 and np.percentile(errs, 90) < 0.025
+    assert np.median(shifts) > 5 * np.median(errs)
