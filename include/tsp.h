@@ -58,6 +58,9 @@ typedef struct {
     double cut;        /* window radius in units of sigma; 0 selects 3 (Sec. 3) */
     int32_t flags;     /* reserved, must be 0 */
     int32_t reserved;
+    double gamma;      /* cross term of C^-1 between z_u (z_d) and delta_l (Sec. 3):
+                          C^-1 = [[1/sz^2, 0, g], [0, 1/sz^2, -g], [g, -g, 1/sdl^2]];
+                          0 = diagonal; finite with 2 g^2 < 1/(sz^2 sdl^2) */
 } tsp_params;
 
 /* Counters of the last upload / pass (filled by tsp_stats). */

@@ -77,40 +77,7 @@ int plan(tsp_ctx* c)
     const double dy = p.dy > 0 ? p.dy : 2.0 * p.R / p.ny;
     const double dz = p.dz > 0 ? p.dz : p.L / p.nz;
     const double cut = p.cut > 0 ? p.cut : 3.0;
-    const double iz = 1.0 / (p.sigma_z * p.sigma_z), il = 1.0 / (p.sigma_dl * p.sigma_dl);
-    const double log2e = 1.4426950408889634;
-    const double pi = 3.14159265358979323846;
-    Geo& g = c->g;
-    g.ny = p.ny;
-    g.nz = p.nz;
-    g.dy = (float)dy;
-    g.dz = (float)dz;
-    g.inv_dy = (float)(1.0 / dy);
-    g.inv_dz = (float)(1.0 / dz);
-    g.y0 = (float)(-p.R + 0.5 * dy);
-    g.z0 = (float)(-0.5 * p.L + 0.5 * dz);
-    g.R = (float)p.R;
-    g.iz = (float)iz;
-    g.il = (float)il;
-    g.cut2 = (float)(cut * cut);
-    g.hy_coef = (float)(cut * p.sigma_dl / 2.0);
-    g.hz_a = (float)(cut * cut * p.sigma_z * p.sigma_z / 2.0);
-    g.hz_b = (float)(cut * cut * p.sigma_dl * p.sigma_dl / 4.0);
-    // reading R4: K = det^(1/2)(C^-1) / (2 pi^2), det(C^-1) = iz^2 il
-    g.log2K = (float)std::log2(iz * std::sqrt(il) / (2.0 * pi * pi));
-    g.ksu = (float)std::sqrt(log2e * iz);
-    g.kA = (float)std::sqrt(log2e / 2.0);
-    g.half_log2e = (float)(log2e / 2.0);
-    g.inv_sqrt_2iz = (float)(1.0 / std::sqrt(2.0 * iz));
-    g.y0d = -p.R + 0.5 * dy;
-    g.z0d = -0.5 * p.L + 0.5 * dz;
-    g.dyd = dy;
-    g.dzd = dz;
-    g.Rd = p.R;
-    g.izd = iz;
-    g.ild = il;
-    g.cut2d = cut * cut;
-    g.Ld = p.L;
+    c->g = make_geo(p);
 
     // lane capacity: the longest chord of the ellipse is 2 cut sigma_z / sqrt(2)
     const double umax = cut * p.sigma_z / std::sqrt(2.0);
@@ -226,6 +193,8 @@ int validate(const tsp_params* p, tsp_ctx* c)
         return fail(c, TSP_EINVAL, "sigma_z and sigma_dl must be finite and > 0");
     if (!(p->cut == 0.0 || pos(p->cut))) return fail(c, TSP_EINVAL, "cut must be 0 or > 0");
     if (p->flags != 0) return fail(c, TSP_EINVAL, "flags must be 0");
+    if (!cinv_valid(*p))
+        return fail(c, TSP_EINVAL, "gamma must be finite with 2 gamma^2 < 1/(sigma_z^2 sigma_dl^2)");
     return TSP_OK;
 }
 
@@ -741,6 +710,13 @@ int tsp_set_sigma(tsp_ctx* c, double sigma_z, double sigma_dl, void* stream)
     if (!(std::isfinite(sigma_z) && sigma_z > 0 && std::isfinite(sigma_dl) && sigma_dl > 0))
         return fail(c, TSP_EINVAL, "sigmas must be finite and > 0");
     if (c->appending) return fail(c, TSP_ESTATE, "set_sigma between begin_events and end_events");
+    {
+        tsp_params q = c->p;
+        q.sigma_z = sigma_z;
+        q.sigma_dl = sigma_dl;
+        if (!cinv_valid(q))
+            return fail(c, TSP_EINVAL, "sigmas give a C^-1 that is not positive definite with gamma");
+    }
     DeviceGuard dg(c->dev);
     cudaStream_t st = (cudaStream_t)stream;
     tsp_params old = c->p;

@@ -40,6 +40,10 @@ struct Geo {
     float kA;               // sqrt(log2(e) / 2)
     float half_log2e;       // log2(e) / 2
     float inv_sqrt_2iz;     // 1 / sqrt(2 iz)
+    // the cross term gamma of C^-1 (Sec. 3) enters only row constants:
+    //   Q += -gR8 t c2i sec (y + Dy),  aCb += -gR4 c2i sec Dy  (bCb unchanged)
+    float gR8, gR4;         // 8 gamma R, 4 gamma R
+    float ldz, ldl;         // (1/2) d log det(C^-1) / d iz, / d il
     // double-precision copies for the exact window decision near its boundary
     double y0d, z0d, dyd, dzd, Rd, izd, ild, cut2d;
     double Ld;              // strip length
@@ -314,6 +318,7 @@ __device__ __forceinline__ void row_q(const Geo& g, const float4& ev, const Chor
     const float t = ev.z, c2i = ev.w, y = c.y, Dy = c.Dy, y2 = y * y;
     const float aCa = 2.0f * g.iz * (g.R * g.R + y2) * c2i * c2i + 4.0f * g.il * y2 * t * t * c2i;
     Qc = aCa + 4.0f * g.il * y * fmaf(2.0f * t, t, 1.0f) * Dy * c2i;   // Q at u = 0
+    if (g.gR8 != 0.0f) Qc -= g.gR8 * t * c2i * sqrtf(c2i) * (y + Dy);
     gam2 = -4.0f * g.iz * y * t * c2i;                                 // 2 oCb slope
 }
 
@@ -323,6 +328,7 @@ __device__ __forceinline__ void row_acb(const Geo& g, const float4& ev, const Ch
     const float t = ev.z, c2i = ev.w, y = c.y, Dy = c.Dy;
     alpha = -2.0f * g.iz * y * c2i;            // aCb slope in u
     beta = 4.0f * g.il * y * t * Dy * c2i;     // aCb at u = 0
+    if (g.gR4 != 0.0f) beta -= g.gR4 * c2i * sqrtf(c2i) * Dy;
 }
 
 // Bounding box of the event's window in pixel rows and columns, clipped to the

@@ -2,6 +2,7 @@
 // (Eq. 2 and the App. B window), binning of events by image tile, the image
 // update that closes one iteration of Eq. iter, and small reductions.
 #include <climits>
+#include <cmath>
 
 #include "tsp_launch.h"
 
@@ -362,6 +363,59 @@ __global__ void k_check_image(int n, const float* __restrict__ rho, int* bad)
 }
 
 }  // namespace
+
+bool cinv_valid(const tsp_params& p)
+{
+    const double iz = 1.0 / (p.sigma_z * p.sigma_z), il = 1.0 / (p.sigma_dl * p.sigma_dl);
+    return std::isfinite(p.gamma) && 2.0 * p.gamma * p.gamma < iz * il;
+}
+
+Geo make_geo(const tsp_params& p)
+{
+    const double dy = p.dy > 0 ? p.dy : 2.0 * p.R / p.ny;
+    const double dz = p.dz > 0 ? p.dz : p.L / p.nz;
+    const double cut = p.cut > 0 ? p.cut : 3.0;
+    const double iz = 1.0 / (p.sigma_z * p.sigma_z), il = 1.0 / (p.sigma_dl * p.sigma_dl);
+    const double gm = p.gamma;
+    const double log2e = 1.4426950408889634, pi = 3.14159265358979323846;
+    Geo g{};
+    g.ny = p.ny;
+    g.nz = p.nz;
+    g.dy = (float)dy;
+    g.dz = (float)dz;
+    g.inv_dy = (float)(1.0 / dy);
+    g.inv_dz = (float)(1.0 / dz);
+    g.y0 = (float)(-p.R + 0.5 * dy);
+    g.z0 = (float)(-0.5 * p.L + 0.5 * dz);
+    g.R = (float)p.R;
+    g.iz = (float)iz;
+    g.il = (float)il;
+    g.cut2 = (float)(cut * cut);
+    g.hy_coef = (float)(cut * p.sigma_dl / 2.0);
+    g.hz_a = (float)(cut * cut * p.sigma_z * p.sigma_z / 2.0);
+    g.hz_b = (float)(cut * cut * p.sigma_dl * p.sigma_dl / 4.0);
+    // reading R4: K = det^(1/2)(C^-1) / (2 pi^2), det(C^-1) = iz^2 il - 2 iz gamma^2
+    const double det = iz * iz * il - 2.0 * iz * gm * gm;
+    g.log2K = (float)std::log2(std::sqrt(det) / (2.0 * pi * pi));
+    g.ksu = (float)std::sqrt(log2e * iz);
+    g.kA = (float)std::sqrt(log2e / 2.0);
+    g.half_log2e = (float)(log2e / 2.0);
+    g.inv_sqrt_2iz = (float)(1.0 / std::sqrt(2.0 * iz));
+    g.gR8 = (float)(8.0 * gm * p.R);
+    g.gR4 = (float)(4.0 * gm * p.R);
+    g.ldz = (float)((iz * il - gm * gm) / (iz * (iz * il - 2.0 * gm * gm)));
+    g.ldl = (float)(0.5 * iz / (iz * il - 2.0 * gm * gm));
+    g.y0d = -p.R + 0.5 * dy;
+    g.z0d = -0.5 * p.L + 0.5 * dz;
+    g.dyd = dy;
+    g.dzd = dz;
+    g.Rd = p.R;
+    g.izd = iz;
+    g.ild = il;
+    g.cut2d = cut * cut;
+    g.Ld = p.L;
+    return g;
+}
 
 cudaError_t launch_sensitivity(double R, double L, int ny, int nz, double dy, double dz, float* s,
                                cudaStream_t st)

@@ -3,9 +3,15 @@
 
 #include <cuda_runtime.h>
 
+#include "tsp.h"
 #include "tsp_device.cuh"
 
 namespace tsp {
+
+// Kernel constants of a (validated) parameter set (tsp_kernels.cu).
+Geo make_geo(const tsp_params& p);
+// Whether the parameters give a positive-definite C^-1 (2 gamma^2 < iz il).
+bool cinv_valid(const tsp_params& p);
 
 // Lane capacities (pixels of one row segment held in registers) compiled in.
 constexpr int kLmaxList[] = {12, 24, 48, 64};

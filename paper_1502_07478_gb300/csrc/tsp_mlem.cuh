@@ -222,8 +222,8 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const E
         rg.cz0 = -2.0f * y * c2i * u0;
         rg.dcz = -2.0f * y * c2i * g.dz;
         const float Bl = 4.0f * Dy * Dy * c2i;
-        rg.kz = 1.0f / g.iz;
-        rg.kl = 0.5f / g.il - 0.5f * Bl;
+        rg.kz = g.ldz;
+        rg.kl = g.ldl - 0.5f * Bl;
         rg.cl = 4.0f * y * t * Dy * c2i;
         rg.qlh = 2.0f * y2 * t * t * c2i + 2.0f * y * fmaf(2.0f * t, t, 1.0f) * Dy * c2i;
     }

@@ -100,42 +100,12 @@ int geometry(const tsp_params& p, Geo& g, int& lmax, int& nseg, int& G, char* er
     auto pos = [](double v) { return std::isfinite(v) && v > 0.0; };
     if (!pos(p.R) || !pos(p.L) || p.ny <= 0 || p.nz <= 0 || !pos(p.sigma_z) ||
         !pos(p.sigma_dl) || !(p.dy == 0.0 || pos(p.dy)) || !(p.dz == 0.0 || pos(p.dz)) ||
-        !(p.cut == 0.0 || pos(p.cut)) || p.flags != 0)
+        !(p.cut == 0.0 || pos(p.cut)) || p.flags != 0 || !cinv_valid(p))
         return report(errbuf, errlen, TSP_EINVAL, "invalid tsp_params");
     const double dy = p.dy > 0 ? p.dy : 2.0 * p.R / p.ny;
     const double dz = p.dz > 0 ? p.dz : p.L / p.nz;
     const double cut = p.cut > 0 ? p.cut : 3.0;
-    const double iz = 1.0 / (p.sigma_z * p.sigma_z), il = 1.0 / (p.sigma_dl * p.sigma_dl);
-    const double log2e = 1.4426950408889634, pi = 3.14159265358979323846;
-    g.ny = p.ny;
-    g.nz = p.nz;
-    g.dy = (float)dy;
-    g.dz = (float)dz;
-    g.inv_dy = (float)(1.0 / dy);
-    g.inv_dz = (float)(1.0 / dz);
-    g.y0 = (float)(-p.R + 0.5 * dy);
-    g.z0 = (float)(-0.5 * p.L + 0.5 * dz);
-    g.R = (float)p.R;
-    g.iz = (float)iz;
-    g.il = (float)il;
-    g.cut2 = (float)(cut * cut);
-    g.hy_coef = (float)(cut * p.sigma_dl / 2.0);
-    g.hz_a = (float)(cut * cut * p.sigma_z * p.sigma_z / 2.0);
-    g.hz_b = (float)(cut * cut * p.sigma_dl * p.sigma_dl / 4.0);
-    g.log2K = (float)std::log2(iz * std::sqrt(il) / (2.0 * pi * pi));
-    g.ksu = (float)std::sqrt(log2e * iz);
-    g.kA = (float)std::sqrt(log2e / 2.0);
-    g.half_log2e = (float)(log2e / 2.0);
-    g.inv_sqrt_2iz = (float)(1.0 / std::sqrt(2.0 * iz));
-    g.y0d = -p.R + 0.5 * dy;
-    g.z0d = -0.5 * p.L + 0.5 * dz;
-    g.dyd = dy;
-    g.dzd = dz;
-    g.Rd = p.R;
-    g.izd = iz;
-    g.ild = il;
-    g.cut2d = cut * cut;
-    g.Ld = p.L;
+    g = make_geo(p);
     const int need = (int)std::floor(2.0 * cut * p.sigma_z / std::sqrt(2.0) / dz) + 2;
     lmax = 0;
     for (int k = 0; k < kLmaxCount && !lmax; ++k)

@@ -41,6 +41,27 @@ def test_gradient_matches_oracle(prob):
     r.set_sigma(w.sigma_z, w.sigma_dl)
 
 
+def test_gradient_with_gamma_matches_oracle(prob):
+    """The adjoint pass with the cross term gamma of C^-1 (the log-determinant
+    term of d log P / d sigma changes; Q and aC^-1b gain gamma terms)."""
+    from paper_1502_07478_gb300 import Recon
+    w, ev, _, rho = prob
+    gm = 5e-4
+    r = Recon.from_workload(w, gamma=gm)
+    r.upload_events(*ev)
+    r.set_sigma(14.0, 55.0)
+    r.set_image(rho.astype(np.float32))
+    L, g, gs = r.loglik_grad()
+    r.close()
+    st = Setup.from_workload(w, sigma_z=14.0, sigma_dl=55.0, gamma=gm)
+    Lref, gref, gsref = oracle.loglik_grad(st, ev, rho)
+    g = g.cpu().numpy().astype(np.float64).ravel()
+    gref = np.asarray(gref).ravel()
+    assert L == pytest.approx(Lref, rel=1e-6)
+    assert np.linalg.norm(g - gref) / np.linalg.norm(gref) <= 1e-4
+    np.testing.assert_allclose(gs, gsref, rtol=1e-3)
+
+
 def test_sigma_gradient_matches_fp64_differences(prob):
     """GPU g_sigma against FP64 central differences of the oracle's L (h = 1e-3
     relative, windows frozen at the base sigma)."""

@@ -261,3 +261,23 @@ def test_thread_granularity_variant_matches_tiles_1mm():
         out.append(r.read_image(out=np.empty((w.ny, w.nz), np.float32)))
         r.close()
     assert rel_err(out[1], out[0].astype(np.float64)) <= 1e-5
+
+
+def test_gamma_cross_term_parity(small):
+    """C^-1 with the cross term gamma (Sec. 3): the GPU image follows the
+    oracle with the same gamma, and differs from the diagonal result."""
+    w, ev = small
+    gm = 5e-4
+    r = _recon(w, gamma=gm)
+    r.upload_events(*ev)
+    r.iterate(5)
+    img = r.read_image(out=np.empty((w.ny, w.nz), np.float32))
+    L = r.loglik()
+    r.close()
+    st = Setup.from_workload(w, gamma=gm)
+    ref, _ = oracle.mlem(st, ev, 5)
+    assert rel_err(img, ref) <= TOL
+    ref0, _ = oracle.mlem(Setup.from_workload(w), ev, 5)
+    assert rel_err(ref, ref0) > 100 * TOL
+    Lref = oracle.loglik_grad(st, ev, img, want_rho=False, want_sigma=False)[0]
+    assert L == pytest.approx(Lref, rel=1e-6)
