@@ -103,7 +103,7 @@ int plan(tsp_ctx* c)
     const int maxrows = (int)std::floor(2.0 * hy / dy) + 2;
     c->maxrows = maxrows;
     c->G = c->nseg * ((maxrows + 31) / 32);
-    if (c->G > kWarps) return fail(c, TSP_EINVAL, "window has more rows than one block can hold");
+    if (c->G > kMinWarps) return fail(c, TSP_EINVAL, "window has more rows than one block can hold");
 
     // tiling (see Tiling): angle bins of width 1/16 in tan(theta~) cover the
     // accepted range |t| <= L/2R widened by 6 sigma of its measurement noise
@@ -152,7 +152,7 @@ int plan(tsp_ctx* c)
             c->lmax = l2;
             c->nseg = 2;
             c->G = 2 * ((maxrows + 31) / 32);
-            if (c->G > kWarps)
+            if (c->G > kMinWarps)
                 return fail(c, TSP_EINVAL, "window has more rows than one block can hold");
         } else {
             tl.nb = 0;

@@ -135,7 +135,7 @@ int rebuild(tsp_batch* b, cudaStream_t st)
     for (int i = 0; i < k; ++i) {
         tsp_ctx* c = b->inst[i];
         const int G = nseg * ((c->maxrows + 31) / 32);
-        if (G > kWarps) return bfail(b, TSP_EINVAL, "window has more rows than one block can hold");
+        if (G > kMinWarps) return bfail(b, TSP_EINVAL, "window has more rows than one block can hold");
         Inst& t = table[i];
         std::memset(&t, 0, sizeof(Inst));
         t.g = c->g;

@@ -19,11 +19,26 @@
 
 namespace tsp {
 
-constexpr int kThreads = 512;          // threads per persistent block (16 warps)
-constexpr int kWarps = kThreads / 32;
 constexpr int kPadFloats = 128;        // slack after image-sized buffers (>= max LMAX)
 
 enum Mode : int { kMlem = 0, kLoglik = 1, kGrad = 2 };
+
+// Threads per persistent block of the passes: for the plain one-lane-per-row
+// MLEM and log-likelihood passes as many warps as the register file holds for
+// the lane capacity LMAX (the P cache takes LMAX registers per thread, 65536
+// registers per SM); the gradient pass, the two-lanes-per-row passes and the
+// batched passes keep more state per thread and stay at 512 (more threads
+// would spill).  A group of G <= kMinWarps warps always fits, and a block
+// never has more than 15 groups of two or more warps (one named barrier each,
+// ids 1..15).
+__host__ __device__ constexpr int pass_threads(int lmax, int mode, int nseg, bool batch)
+{
+    return (mode == kGrad || nseg != 1 || batch)
+               ? 512
+               : (lmax <= 12 ? 960 : lmax <= 24 ? 768 : lmax <= 48 ? 640 : 512);
+}
+constexpr int kMinWarps = 16;
+constexpr int kMaxWarps = 30;
 
 // Per-reconstruction constants, passed by value to the kernels.
 struct Geo {
@@ -83,18 +98,18 @@ __device__ __forceinline__ int row_shift(const Tiling& tl, float shear, int iy)
 
 // Shared-memory layout of the tile kernel, in floats: kPadFloats slack, the
 // rho' region (RH*RS), 2*kPadFloats slack, the accumulator region (RH*RS),
-// kPadFloats slack, then the groups' reduction slots (kWarps/G groups x 2
-// parities x 3G floats <= 6*kWarps).
+// kPadFloats slack, then the groups' reduction slots (warps/G groups x 2
+// parities x 3G floats <= 6*kMaxWarps).
 __host__ __device__ constexpr size_t tiles_smem_floats(int RH, int RS)
 {
     return (size_t)kPadFloats + (size_t)RH * RS + 2 * kPadFloats + (size_t)RH * RS + kPadFloats +
-           6 * kWarps;
+           6 * kMaxWarps;
 }
 
 // The same with only the accumulator staged (rho' read from global memory).
 __host__ __device__ constexpr size_t tiles_acc_smem_floats(int RH, int RS)
 {
-    return (size_t)kPadFloats + (size_t)RH * RS + kPadFloats + 6 * kWarps;
+    return (size_t)kPadFloats + (size_t)RH * RS + kPadFloats + 6 * kMaxWarps;
 }
 
 // Device-side accumulators of one pass.

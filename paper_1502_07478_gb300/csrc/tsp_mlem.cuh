@@ -512,10 +512,12 @@ __device__ __forceinline__ Frame tile_frame(const Geo& g, const Tiling& tl, int 
 // GLD: only the accumulator is staged (windows too large for both regions);
 // rho' is read from the global image through the read-only cache.
 template <int LMAX, int MODE, int NSEG, bool BATCH, bool GLD = false>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(pass_threads(LMAX, MODE, NSEG, BATCH), 1)
 k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, int n_items,
         int* queue)
 {
+    constexpr int kThreads = pass_threads(LMAX, MODE, NSEG, BATCH);
+    constexpr int kWarps = kThreads / 32;
     extern __shared__ float4 smem_f4[];
     float* const smem = reinterpret_cast<float*>(smem_f4);
     __shared__ int s_item;
@@ -625,10 +627,11 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
 // Events whose window does not fit their tile's region: same evaluation, with
 // rho' read from global memory and the scatter done by global atomics.
 template <int LMAX, int MODE, int NSEG>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(pass_threads(LMAX, MODE, NSEG, false), 1)
 k_outliers(Geo g, EventsView evs, int first, int count, const float* __restrict__ rhop,
            float* __restrict__ A, Accum* accum, int G)
 {
+    constexpr int kWarps = pass_threads(LMAX, MODE, NSEG, false) / 32;
     __shared__ float s_part[kWarps * 2 * 3];
     __shared__ Frame s_frame;
     __shared__ BlockSums s_sums;
@@ -660,9 +663,11 @@ k_outliers(Geo g, EventsView evs, int first, int count, const float* __restrict_
 // Batched outlier kernel: items (-1, first, count, reconstruction), one block
 // per item at a time.
 template <int LMAX, int MODE, int NSEG>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(pass_threads(LMAX, MODE, NSEG, true), 1)
 k_outliers_batch(const Inst* __restrict__ table, const int4* __restrict__ items, int n_items)
 {
+    constexpr int kThreads = pass_threads(LMAX, MODE, NSEG, true);
+    constexpr int kWarps = kThreads / 32;
     __shared__ float s_part[kWarps * 2 * 3];
     __shared__ Frame s_frame;
     __shared__ BlockSums s_sums;

@@ -25,14 +25,15 @@ cudaError_t run_pass(const PassArgs& a, cudaStream_t st)
         p.accum = a.accum;
         p.G = a.G;
         p.pad = 0;
-        k_tiles<LMAX, MODE, NSEG, false, GLD><<<a.grid, kThreads, a.smem, st>>>(
+        k_tiles<LMAX, MODE, NSEG, false, GLD>
+            <<<a.grid, pass_threads(LMAX, MODE, NSEG, false), a.smem, st>>>(
             p, nullptr, a.items, a.n_items, &a.accum->queue);
     }
     if (a.outlier_count > 0) {
-        const int per_block = kWarps / a.G;
+        const int per_block = pass_threads(LMAX, MODE, NSEG, false) / 32 / a.G;
         int blocks = (a.outlier_count + per_block - 1) / per_block;
         if (blocks > a.grid) blocks = a.grid;
-        k_outliers<LMAX, MODE, NSEG><<<blocks, kThreads, 0, st>>>(
+        k_outliers<LMAX, MODE, NSEG><<<blocks, pass_threads(LMAX, MODE, NSEG, false), 0, st>>>(
             a.g, a.evs, a.outlier_first, a.outlier_count, a.rhop, a.A, a.accum, a.G);
     }
     return cudaGetLastError();
@@ -56,11 +57,13 @@ cudaError_t run_batch(const BatchArgs& a, cudaStream_t st)
 {
     Inst none{};
     if (a.n_items > 0)
-        k_tiles<LMAX, MODE, NSEG, true><<<a.grid, kThreads, a.smem, st>>>(none, a.table, a.items,
+        k_tiles<LMAX, MODE, NSEG, true><<<a.grid, pass_threads(LMAX, MODE, NSEG, true), a.smem, st>>>(
+            none, a.table, a.items,
                                                                           a.n_items, a.queue);
     if (a.n_outlier_items > 0)
         k_outliers_batch<LMAX, MODE, NSEG>
-            <<<a.n_outlier_items < a.grid ? a.n_outlier_items : a.grid, kThreads, 0, st>>>(
+            <<<a.n_outlier_items < a.grid ? a.n_outlier_items : a.grid,
+               pass_threads(LMAX, MODE, NSEG, true), 0, st>>>(
                 a.table, a.outlier_items, a.n_outlier_items);
     return cudaGetLastError();
 }

@@ -121,7 +121,7 @@ int geometry(const tsp_params& p, Geo& g, int& lmax, int& nseg, int& G, char* er
     if (!lmax) return report(errbuf, errlen, TSP_EINVAL, "window chords too long");
     const int maxrows = (int)std::floor(2.0 * cut * p.sigma_dl / 2.0 * 1.00001 / dy) + 2;
     G = nseg * ((maxrows + 31) / 32);
-    if (G > kWarps) return report(errbuf, errlen, TSP_EINVAL, "window has too many rows");
+    if (G > kMinWarps) return report(errbuf, errlen, TSP_EINVAL, "window has too many rows");
     return TSP_OK;
 }
 
