@@ -223,12 +223,13 @@ int tsp_autotune(tsp_ctx* ctx, tsp_schedule* chosen, float* best_ms, void* strea
 
 /* ------------------------------------------------------------------------
  * Batches: k independent reconstructions (each with its own geometry, grid,
- * resolution, events and image) advanced together.  Each MLEM iteration of a
- * batch is three kernel launches whatever k: a reset of the pass
- * accumulators, one persistent tile pass over the work items of every
- * reconstruction (plus one launch for outlier events when some
- * reconstruction has them), and the image update of all reconstructions;
- * n iterations are replayed from one CUDA graph.  Results equal those of k
+ * resolution, events and image) advanced together.  An MLEM iteration of a
+ * batch is, whatever k: a reset of the pass accumulators, one persistent tile
+ * launch per kernel class present (the reconstructions whose windows need the
+ * same lane capacity and row split share one launch over all their work
+ * items; plus one launch for outlier events when some reconstruction of the
+ * class has them), and the image update of all reconstructions; n iterations
+ * are replayed from one CUDA graph.  Results equal those of k
  * separate contexts up to float rounding order.  A batch is not thread-safe.
  * Indices i are 0..k-1; an index out of range gives TSP_EINVAL. */
 typedef struct tsp_batch tsp_batch;

@@ -1,12 +1,14 @@
 // libtsp batched entry points: many independent reconstructions advanced
 // together.  Each reconstruction keeps its own context (geometry, resolution,
 // grid, events, images); the batch adds a device table of their Inst records,
-// one merged list of work items, and CUDA graphs in which every iteration of
-// Eq. iter is three launches whatever the batch size: reset of the pass
-// accumulators, one persistent tile pass over the items of all
-// reconstructions (plus the batched outlier kernel when some events need it),
-// and the per-pixel update of all images.  The tile schedule (tile height,
-// items per SM, item order) is chosen by a measuring autotuner.
+// merged lists of work items, and CUDA graphs in which an iteration of Eq. iter
+// is a reset of the pass accumulators, persistent tile passes over the items of
+// all reconstructions, and the per-pixel update of all images -- whatever the
+// batch size.  The reconstructions are grouped by the tile kernel their
+// windows need (lane capacity and row split, which also fix its block size):
+// one persistent launch per group present (plus the batched outlier kernel when
+// some events need it).  The tile schedule (tile height, items per SM, item
+// order) is chosen by a measuring autotuner.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -19,20 +21,29 @@
 using namespace tsp;
 using namespace tsp_host;
 
+// The reconstructions of a batch that share one tile kernel (lane capacity
+// lmax, row split nseg): their merged work items and outlier items.
+struct BatchClass {
+    int lmax = 0, nseg = 1;
+    size_t smem = 0;
+    int4* items = nullptr;
+    int4* oitems = nullptr;
+    int n_items = 0, n_oitems = 0, items_cap = 0, oitems_cap = 0;
+};
+
+constexpr int kMaxClasses = 2 * kLmaxCount;
+
 struct tsp_batch {
     std::vector<tsp_ctx*> inst;
     int dev = 0, num_sms = 0;
     Schedule sched;
     bool dirty = true;
-    int lmax = 0, nseg = 1;
-    size_t smem = 0;
     int max_npix = 0;
     Inst* table = nullptr;
     BatchImg* imgs = nullptr;
-    int4* items = nullptr;
-    int4* oitems = nullptr;
-    int n_items = 0, n_oitems = 0, items_cap = 0, oitems_cap = 0;
-    int* queue = nullptr;
+    BatchClass cls[kMaxClasses];
+    int n_cls = 0;
+    int* queue = nullptr;       // one work counter per class
     cudaStream_t cap_stream = nullptr;
     std::map<int, tsp_ctx::Graph> graphs;
     int last_graph = -1;
@@ -113,29 +124,24 @@ int rebuild(tsp_batch* b, cudaStream_t st)
         if (!b->inst[i]->uploaded)
             return bfail(b, TSP_ESTATE,
                          "reconstruction " + std::to_string(i) + " has no uploaded events");
-    int need = 0, need2 = 0;
-    for (tsp_ctx* c : b->inst) {
-        need = std::max(need, c->need);
-        need2 = std::max(need2, c->need / 2 + 2);
-    }
-    int lmax = 0, nseg = 1;
-    for (int q = 0; q < kLmaxCount && !lmax; ++q)
-        if (kLmaxList[q] >= need) lmax = kLmaxList[q];
-    if (!lmax) {
-        nseg = 2;
-        for (int q = 0; q < kLmaxCount && !lmax; ++q)
-            if (kLmaxList[q] >= need2) lmax = kLmaxList[q];
-    }
-    if (!lmax) return bfail(b, TSP_EINVAL, "window chords too long for the compiled lane capacities");
     std::vector<Inst> table(k);
     std::vector<BatchImg> imgs(k);
-    size_t smem = 0;
     int max_npix = 0;
     long long placed = 0;
+    // kernel class of every reconstruction: its own lane capacity and row split
+    int n_cls = 0;
+    int cls_lmax[kMaxClasses], cls_nseg[kMaxClasses];
+    std::vector<int> cls_of(k);
     for (int i = 0; i < k; ++i) {
         tsp_ctx* c = b->inst[i];
-        const int G = nseg * ((c->maxrows + 31) / 32);
-        if (G > kMinWarps) return bfail(b, TSP_EINVAL, "window has more rows than one block can hold");
+        int q = 0;
+        while (q < n_cls && !(cls_lmax[q] == c->lmax && cls_nseg[q] == c->nseg)) ++q;
+        if (q == n_cls) {
+            cls_lmax[q] = c->lmax;
+            cls_nseg[q] = c->nseg;
+            ++n_cls;
+        }
+        cls_of[i] = q;
         Inst& t = table[i];
         std::memset(&t, 0, sizeof(Inst));
         t.g = c->g;
@@ -146,7 +152,7 @@ int rebuild(tsp_batch* b, cudaStream_t st)
         t.rhop = c->rhop;
         t.A = c->A;
         t.accum = c->accum;
-        t.G = G;
+        t.G = c->G;
         BatchImg& m = imgs[i];
         m.rho = c->rho;
         m.rhop = c->rhop;
@@ -156,109 +162,132 @@ int rebuild(tsp_batch* b, cudaStream_t st)
         m.accum = c->accum;
         m.npix = c->npix;
         m.pad = 0;
-        smem = std::max(smem, c->smem);
         max_npix = std::max(max_npix, c->npix);
         if (!c->bin_cnt.empty())
             placed += std::accumulate(c->bin_cnt.begin(), c->bin_cnt.end() - 1, 0ll);
     }
     // items: tile runs of at most E events, E from the whole batch's load
     const long long E = item_events(placed, b->sched.items_per_sm, b->num_sms);
-    std::vector<std::vector<int4>> lists(k);
-    std::vector<int4> outl;
-    for (int i = 0; i < k; ++i) {
-        const tsp_ctx* c = b->inst[i];
-        // a reconstruction whose tiles stage only the accumulator is not
-        // supported by the batched tile kernel: all its events take the
-        // batched global-memory path
-        long long first = c->outlier_first, count = c->n_outliers;
-        if (c->gld) {
-            first = 0;
-            count = c->outlier_first + c->n_outliers;
-        } else {
-            lists[i] = tile_items(c, E, i);
-        }
-        for (long long j = 0; j < count; j += 64)
-            outl.push_back(make_int4(-1, (int)(first + j), (int)std::min<long long>(64, count - j),
-                                     i));
-    }
-    std::vector<int4> items;
-    if (b->sched.order == 0) {
-        // longest estimated item first: events x window pixels, plus the
-        // staging of the item's region
-        std::vector<std::pair<double, int4>> cost;
-        for (int i = 0; i < k; ++i) {
-            const double w = window_pixels(b->inst[i]);
-            const double stage = 0.25 * b->inst[i]->tl.RH * b->inst[i]->tl.RS;
-            for (const int4& it : lists[i]) cost.emplace_back(it.z * w + stage, it);
-        }
-        std::stable_sort(cost.begin(), cost.end(),
-                         [](const auto& x, const auto& y) { return x.first > y.first; });
-        items.reserve(cost.size());
-        for (const auto& x : cost) items.push_back(x.second);
-    } else {
-        for (size_t j = 0;; ++j) {
-            bool any = false;
-            for (int i = 0; i < k; ++i)
-                if (j < lists[i].size()) {
-                    items.push_back(lists[i][j]);
-                    any = true;
-                }
-            if (!any) break;
-        }
-    }
     const size_t limit = dyn_smem_limit(b->dev);
-    if (smem > limit) return bfail(b, TSP_EINVAL, "tile region exceeds the shared memory");
-    BATCH_CUDA(b, prepare_batch_pass(lmax, limit));
-    if ((int)items.size() > b->items_cap) {
-        dfree(b->items);
-        BATCH_CUDA(b, cudaMalloc(&b->items, sizeof(int4) * items.size()));
-        b->items_cap = (int)items.size();
+    for (int q = 0; q < n_cls; ++q) {
+        BatchClass& bc = b->cls[q];
+        bc.lmax = cls_lmax[q];
+        bc.nseg = cls_nseg[q];
+        bc.smem = 0;
+        std::vector<std::vector<int4>> lists;
+        std::vector<int> members;
+        std::vector<int4> outl;
+        for (int i = 0; i < k; ++i) {
+            if (cls_of[i] != q) continue;
+            const tsp_ctx* c = b->inst[i];
+            bc.smem = std::max(bc.smem, c->smem);
+            members.push_back(i);
+            // a reconstruction whose tiles stage only the accumulator is not
+            // supported by the batched tile kernel: all its events take the
+            // batched global-memory path
+            long long first = c->outlier_first, count = c->n_outliers;
+            if (c->gld) {
+                first = 0;
+                count = c->outlier_first + c->n_outliers;
+                lists.emplace_back();
+            } else {
+                lists.push_back(tile_items(c, E, i));
+            }
+            for (long long j = 0; j < count; j += 64)
+                outl.push_back(make_int4(-1, (int)(first + j),
+                                         (int)std::min<long long>(64, count - j), i));
+        }
+        std::vector<int4> items;
+        if (b->sched.order == 0) {
+            // longest estimated item first: events x window pixels, plus the
+            // staging of the item's region
+            std::vector<std::pair<double, int4>> cost;
+            for (size_t m = 0; m < members.size(); ++m) {
+                const tsp_ctx* c = b->inst[members[m]];
+                const double w = window_pixels(c);
+                const double stage = 0.25 * c->tl.RH * c->tl.RS;
+                for (const int4& it : lists[m]) cost.emplace_back(it.z * w + stage, it);
+            }
+            std::stable_sort(cost.begin(), cost.end(),
+                             [](const auto& x, const auto& y) { return x.first > y.first; });
+            items.reserve(cost.size());
+            for (const auto& x : cost) items.push_back(x.second);
+        } else {
+            for (size_t j = 0;; ++j) {
+                bool any = false;
+                for (const auto& l : lists)
+                    if (j < l.size()) {
+                        items.push_back(l[j]);
+                        any = true;
+                    }
+                if (!any) break;
+            }
+        }
+        if (bc.smem > limit) return bfail(b, TSP_EINVAL, "tile region exceeds the shared memory");
+        BATCH_CUDA(b, prepare_batch_pass(bc.lmax, limit));
+        if ((int)items.size() > bc.items_cap) {
+            dfree(bc.items);
+            BATCH_CUDA(b, cudaMalloc(&bc.items, sizeof(int4) * items.size()));
+            bc.items_cap = (int)items.size();
+        }
+        if ((int)outl.size() > bc.oitems_cap) {
+            dfree(bc.oitems);
+            BATCH_CUDA(b, cudaMalloc(&bc.oitems, sizeof(int4) * outl.size()));
+            bc.oitems_cap = (int)outl.size();
+        }
+        if (!items.empty())
+            BATCH_CUDA(b, cudaMemcpyAsync(bc.items, items.data(), sizeof(int4) * items.size(),
+                                          cudaMemcpyHostToDevice, st));
+        if (!outl.empty())
+            BATCH_CUDA(b, cudaMemcpyAsync(bc.oitems, outl.data(), sizeof(int4) * outl.size(),
+                                          cudaMemcpyHostToDevice, st));
+        bc.n_items = (int)items.size();
+        bc.n_oitems = (int)outl.size();
+        BATCH_CUDA(b, cudaStreamSynchronize(st));   // the host vectors go out of scope
     }
-    if ((int)outl.size() > b->oitems_cap) {
-        dfree(b->oitems);
-        BATCH_CUDA(b, cudaMalloc(&b->oitems, sizeof(int4) * outl.size()));
-        b->oitems_cap = (int)outl.size();
-    }
-    if (!items.empty())
-        BATCH_CUDA(b, cudaMemcpyAsync(b->items, items.data(), sizeof(int4) * items.size(),
-                                      cudaMemcpyHostToDevice, st));
-    if (!outl.empty())
-        BATCH_CUDA(b, cudaMemcpyAsync(b->oitems, outl.data(), sizeof(int4) * outl.size(),
-                                      cudaMemcpyHostToDevice, st));
     BATCH_CUDA(b, cudaMemcpyAsync(b->table, table.data(), sizeof(Inst) * k,
                                   cudaMemcpyHostToDevice, st));
     BATCH_CUDA(b, cudaMemcpyAsync(b->imgs, imgs.data(), sizeof(BatchImg) * k,
                                   cudaMemcpyHostToDevice, st));
     BATCH_CUDA(b, cudaStreamSynchronize(st));
-    b->n_items = (int)items.size();
-    b->n_oitems = (int)outl.size();
-    b->lmax = lmax;
-    b->nseg = nseg;
-    b->smem = smem;
+    b->n_cls = n_cls;
     b->max_npix = max_npix;
     clear_batch_graphs(b);
     b->dirty = false;
     return TSP_OK;
 }
 
-BatchArgs batch_args(const tsp_batch* b)
+BatchArgs batch_args(const tsp_batch* b, int q)
 {
+    const BatchClass& bc = b->cls[q];
     BatchArgs a;
     a.table = b->table;
-    a.items = b->items;
-    a.n_items = b->n_items;
-    a.outlier_items = b->oitems;
-    a.n_outlier_items = b->n_oitems;
-    a.queue = b->queue;
-    a.nseg = b->nseg;
+    a.items = bc.items;
+    a.n_items = bc.n_items;
+    a.outlier_items = bc.oitems;
+    a.n_outlier_items = bc.n_oitems;
+    a.queue = b->queue + q;
+    a.nseg = bc.nseg;
     a.grid = b->num_sms;
-    a.smem = b->smem;
+    a.smem = bc.smem;
     return a;
 }
 
 long long batch_pass_launches(const tsp_batch* b)
 {
-    return (b->n_items > 0 ? 1 : 0) + (b->n_oitems > 0 ? 1 : 0);
+    long long n = 0;
+    for (int q = 0; q < b->n_cls; ++q)
+        n += (b->cls[q].n_items > 0 ? 1 : 0) + (b->cls[q].n_oitems > 0 ? 1 : 0);
+    return n;
+}
+
+// One batched pass (MODE kMlem or kGrad): the tile passes of every class.
+cudaError_t launch_batch_passes(const tsp_batch* b, int mode, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < b->n_cls && e == cudaSuccess; ++q)
+        e = launch_batch_pass(b->cls[q].lmax, mode, batch_args(b, q), st);
+    return e;
 }
 
 int capture_batch(tsp_batch* b, int n_iter, tsp_ctx::Graph* out)
@@ -272,13 +301,12 @@ int capture_batch(tsp_batch* b, int n_iter, tsp_ctx::Graph* out)
     }
     cudaGraph_t graph = nullptr;
     BATCH_CUDA(b, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    const BatchArgs a = batch_args(b);
     cudaError_t e = cudaSuccess;
     for (int it = 0; it < n_iter && e == cudaSuccess; ++it) {
-        e = launch_batch_begin(b->imgs, k, b->queue, cs);
+        e = launch_batch_begin(b->imgs, k, b->queue, b->n_cls, cs);
         if (e == cudaSuccess && b->profiling)
             e = cudaEventRecordWithFlags(ev[2 * it], cs, cudaEventRecordExternal);
-        if (e == cudaSuccess) e = launch_batch_pass(b->lmax, kMlem, a, cs);
+        if (e == cudaSuccess) e = launch_batch_passes(b, kMlem, cs);
         if (e == cudaSuccess && b->profiling)
             e = cudaEventRecordWithFlags(ev[2 * it + 1], cs, cudaEventRecordExternal);
         if (e == cudaSuccess) e = launch_batch_pixels(b->imgs, k, b->max_npix, 0, cs);
@@ -333,16 +361,15 @@ int time_batch_pass(tsp_batch* b, int reps, float* ms, cudaStream_t st)
         if (rc) return rc;
     }
     const int k = (int)b->inst.size();
-    const BatchArgs a = batch_args(b);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     BATCH_CUDA(b, cudaEventCreate(&e0));
     BATCH_CUDA(b, cudaEventCreate(&e1));
     float best = 1e30f;
     cudaError_t e = cudaSuccess;
     for (int r = 0; r < reps && e == cudaSuccess; ++r) {
-        e = launch_batch_begin(b->imgs, k, b->queue, st);
+        e = launch_batch_begin(b->imgs, k, b->queue, b->n_cls, st);
         if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-        if (e == cudaSuccess) e = launch_batch_pass(b->lmax, kMlem, a, st);
+        if (e == cudaSuccess) e = launch_batch_passes(b, kMlem, st);
         if (e == cudaSuccess) e = cudaEventRecord(e1, st);
         if (e == cudaSuccess) e = launch_batch_pixels(b->imgs, k, b->max_npix, 3, st);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -403,8 +430,8 @@ int tsp_batch_create(const tsp_params* params, int k, tsp_batch** out)
     }
     cudaError_t e = cudaMalloc(&b->table, sizeof(Inst) * k);
     if (e == cudaSuccess) e = cudaMalloc(&b->imgs, sizeof(BatchImg) * k);
-    if (e == cudaSuccess) e = cudaMalloc(&b->queue, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(b->queue, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->queue, sizeof(int) * kMaxClasses);
+    if (e == cudaSuccess) e = cudaMemset(b->queue, 0, sizeof(int) * kMaxClasses);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         b->err = std::string("tsp_batch_create: ") + cudaGetErrorString(e);
@@ -423,8 +450,10 @@ void tsp_batch_destroy(tsp_batch* b)
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     dfree(b->table);
     dfree(b->imgs);
-    dfree(b->items);
-    dfree(b->oitems);
+    for (BatchClass& bc : b->cls) {
+        dfree(bc.items);
+        dfree(bc.oitems);
+    }
     dfree(b->queue);
     for (tsp_ctx* c : b->inst) tsp_destroy(c);
     delete b;
@@ -511,9 +540,9 @@ int tsp_batch_loglik_grad(tsp_batch* b, double* L_out, double* g_sigma, void* st
     int rc;
     if (b->dirty && (rc = rebuild(b, st))) return rc;
     const int k = (int)b->inst.size();
-    BATCH_CUDA(b, launch_batch_begin(b->imgs, k, b->queue, st));
+    BATCH_CUDA(b, launch_batch_begin(b->imgs, k, b->queue, b->n_cls, st));
     BATCH_CUDA(b, launch_batch_pixels(b->imgs, k, b->max_npix, 1, st));
-    BATCH_CUDA(b, launch_batch_pass(b->lmax, kGrad, batch_args(b), st));
+    BATCH_CUDA(b, launch_batch_passes(b, kGrad, st));
     BATCH_CUDA(b, launch_batch_pixels(b->imgs, k, b->max_npix, 2, st));
     b->launches += 3 + batch_pass_launches(b);
     std::vector<Accum> h(k);

@@ -262,7 +262,7 @@ __global__ void k_set_rhop(int npix, const float* __restrict__ rho, const float*
 // Batched forms of k_begin and of the per-pixel kernels: blockIdx.y selects
 // the reconstruction.  op 0 = end of an MLEM iteration (k_finalize), 1 = rho'
 // refresh (k_set_rhop), 2 = gradient (k_grad_finalize), 3 = A <- 0.
-__global__ void k_batch_begin(const BatchImg* __restrict__ im, int k, int* queue)
+__global__ void k_batch_begin(const BatchImg* __restrict__ im, int k, int* queue, int nq)
 {
     for (int i = threadIdx.x; i < k; i += blockDim.x) {
         Accum* a = im[i].accum;
@@ -275,7 +275,7 @@ __global__ void k_batch_begin(const BatchImg* __restrict__ im, int k, int* queue
         a->sum_rhop = 0.0;
         a->queue = 0;
     }
-    if (threadIdx.x == 0) *queue = 0;
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) queue[q] = 0;
 }
 
 __global__ void k_batch_pixels(const BatchImg* __restrict__ im, int op)
@@ -516,9 +516,9 @@ cudaError_t launch_check_image(int n, const float* rho, int* bad, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_begin(const BatchImg* im, int k, int* queue, cudaStream_t st)
+cudaError_t launch_batch_begin(const BatchImg* im, int k, int* queue, int nq, cudaStream_t st)
 {
-    k_batch_begin<<<1, kAuxThreads, 0, st>>>(im, k, queue);
+    k_batch_begin<<<1, kAuxThreads, 0, st>>>(im, k, queue, nq);
     return cudaGetLastError();
 }
 

@@ -97,7 +97,7 @@ cudaError_t launch_finalize(int npix, float* rho, float* rhop, float* A, const f
 cudaError_t launch_grad_finalize(int npix, float* g, float* A, const float* s, cudaStream_t st);
 cudaError_t launch_set_rhop(int npix, const float* rho, const float* s, float* rhop, Accum* accum,
                             cudaStream_t st);
-cudaError_t launch_batch_begin(const BatchImg* im, int k, int* queue, cudaStream_t st);
+cudaError_t launch_batch_begin(const BatchImg* im, int k, int* queue, int nq, cudaStream_t st);
 cudaError_t launch_batch_pixels(const BatchImg* im, int k, int max_npix, int op, cudaStream_t st);
 // Thread-granularity MLEM pass over the n binned events (tsp_thread.cu).
 cudaError_t launch_thread_pass(const Geo& g, const EventsView& evs, int n, const float* rhop,
