@@ -11,8 +11,8 @@ in HBM.  value = events x iterations x steps / time of the timed steps.
 Also reported: batched vs plain on the batched workload (64 reconstructions
 with their own grids, resolutions and event counts, 10 iterations each; one
 tsp_batch with the autotuned schedule against 64 plain contexts run one after
-another, images compared), the same metric end to end through the C ABI with
-host buffers
+another, images compared), the adjoint pass on the 2 mm workload, the same
+metric end to end through the C ABI with host buffers
 (e2e: pinned-host event upload, per-event preparation and binning, the
 iterations and the image readout, every step), the dominant kernel's achieved
 pixel-evaluation rate against the SFU (MUFU) roofline, and the FP64 CPU oracle
@@ -286,6 +286,32 @@ def _make_events(args):
     name, seed = args
     from synth import make_workload
     return make_workload(name, seed=seed).events()
+
+
+def bench_adjoint(reps: int = 5):
+    """The adjoint workload (350 x 250 at 2 mm, 1e6 events): time of one
+    log-likelihood + gradient pass (L, g_rho, g_sigma; denominators recomputed)
+    at sigma = (14, 55) after 5 MLEM iterations, wall clock around the
+    synchronising call, best of reps."""
+    from paper_1502_07478_gb300 import Recon
+    from synth import make_workload
+    w = make_workload("adjoint_2mm")
+    r = Recon.from_workload(w)
+    r.upload_events(*w.events())
+    r.iterate(5)
+    r.set_sigma(14.0, 55.0)
+    r.loglik_grad()
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        r.loglik_grad()
+        best = min(best, time.perf_counter() - t0)
+    W = r.stats()["n_window"]
+    r.close()
+    return {"workload": w.name, "events": w.n_events, "grid": [w.ny, w.nz],
+            "ms_per_gradient": 1e3 * best, "events_per_s": w.n_events / best,
+            "pixel_evals_per_s": W / best,
+            "includes": "rho' refresh, gradient pass, g = s(A - 1), readout of L and g_sigma"}
 
 
 def bench_stress(args, workload, chunk: int = 10_000_000):
@@ -572,9 +598,10 @@ def main():
                "h2d_bytes_per_step": int(sum(p.numel() * 4 for p in pinned)),
                "d2h_bytes_per_step": int(pinned_out.numel() * 4), "steps": k_e2e}
 
-    batched = None
+    batched = adjoint = None
     if not args.no_batched and ws == 1:
         batched = bench_batched(steps=max(1, min(args.steps, 2)), warmup=1)
+        adjoint = bench_adjoint()
 
     if rank != 0:
         if pg:
@@ -597,6 +624,7 @@ def main():
                    "l2": "inputs larger than L2 (prepared events 24 B x 1e7 = 240 MB)",
                    "parallelism": f"{ws} independent reconstructions" if ws > 1 else "1 GPU"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
+        "adjoint": adjoint,
         "gpu_launches": launches,
         "clocks": clk,
         "checks": {"conservation_rel": cons, "n_used": st1["n_used"],

@@ -15,6 +15,9 @@ from synth import batched_instances, make_workload
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-4
+# the same FP32 arithmetic in another summation order (other kernels, block
+# sizes or work order): agreement to a few float32 roundings per pixel sum
+ORDER_TOL = 2e-5
 
 
 def rel_err(gpu, ref, frac=0.01):
@@ -77,7 +80,7 @@ def test_batch_matches_plain_contexts(mixed):
         r.iterate(3)
         plain = r.read_image(out=np.empty((w.ny, w.nz), np.float32))
         r.close()
-        assert rel_err(imgs[i], plain.astype(np.float64)) <= 1e-5
+        assert rel_err(imgs[i], plain.astype(np.float64)) <= ORDER_TOL
     b.close()
 
 
@@ -99,7 +102,7 @@ def test_iterations_split_and_launch_count(mixed):
     # the work queue hands items to blocks in a run-dependent order, so the
     # float sums agree to rounding only
     for x, y in zip(_images(b1, ws), _images(b2, ws)):
-        assert rel_err(y, x.astype(np.float64)) <= 1e-5
+        assert rel_err(y, x.astype(np.float64)) <= ORDER_TOL
     b1.close()
     b2.close()
 
@@ -116,7 +119,7 @@ def test_schedule_does_not_change_results(mixed, sched):
     assert b2.schedule == sched
     b2.iterate(3)
     for x, y in zip(ref, _images(b2, ws)):
-        assert rel_err(y, x.astype(np.float64)) <= 1e-5
+        assert rel_err(y, x.astype(np.float64)) <= ORDER_TOL
     b.close()
     b2.close()
 
@@ -156,7 +159,7 @@ def test_batch_loglik_grad_matches_plain(mixed):
         Lp, gp, gsp = r.loglik_grad()
         gb = b.read_image(i, which=2)
         assert Lb[i] == pytest.approx(Lp, rel=1e-6)
-        assert float((gb - gp).norm() / gp.norm()) <= 1e-5
+        assert float((gb - gp).norm() / gp.norm()) <= ORDER_TOL
         np.testing.assert_allclose(gsb[i], gsp, rtol=1e-4)
         r.close()
     b.close()
@@ -261,6 +264,6 @@ def test_plain_schedule_and_autotune():
     r2.set_schedule(ty_cap=16, items_per_sm=2)
     r2.upload_events(*ev)
     r2.iterate(2)
-    assert rel_err(r2.read_image().cpu().numpy(), ref.astype(np.float64)) <= 1e-5
+    assert rel_err(r2.read_image().cpu().numpy(), ref.astype(np.float64)) <= ORDER_TOL
     r.close()
     r2.close()
