@@ -23,19 +23,19 @@ constexpr int kPadFloats = 128;        // slack after image-sized buffers (>= ma
 
 enum Mode : int { kMlem = 0, kLoglik = 1, kGrad = 2 };
 
-// Threads per persistent block of the passes: for the one-lane-per-row MLEM
-// and log-likelihood passes as many warps as the register file holds for the
-// lane capacity LMAX (the P cache takes LMAX registers per thread, 65536
-// registers per SM; the batched form spills a few registers there, off the
-// pixel loop, and is still faster than at 512); the gradient pass and the
-// two-lanes-per-row passes keep more state per thread and stay at 512.  A
-// group of G <= kMinWarps warps always fits, and a block never has more than
-// 15 groups of two or more warps (one named barrier each, ids 1..15).
+// Threads per persistent block of the passes: for the one-lane-per-row
+// passes as many warps as the register file holds for the lane capacity LMAX
+// (the P cache takes LMAX registers per thread, 65536 registers per SM; some
+// forms spill a few registers there, off the pixel loop, and are still faster
+// than at 512 threads); the two-lanes-per-row passes hold both half-row
+// traversals and stay at 512.  The mode and the batched form do not change
+// the choice.  A group of G <= kMinWarps warps always fits, and a block never
+// has more than 15 groups of two or more warps (one named barrier each, ids
+// 1..15).
 __host__ __device__ constexpr int pass_threads(int lmax, int mode, int nseg, bool batch)
 {
-    return (void)batch, (mode == kGrad || nseg != 1)
-                            ? 512
-                            : (lmax <= 12 ? 960 : lmax <= 24 ? 768 : lmax <= 48 ? 640 : 512);
+    return (void)mode, (void)batch,
+           nseg != 1 ? 512 : (lmax <= 12 ? 960 : lmax <= 24 ? 768 : lmax <= 48 ? 640 : 512);
 }
 constexpr int kMinWarps = 16;
 constexpr int kMaxWarps = 30;
