@@ -822,11 +822,7 @@ int tsp_set_schedule(tsp_ctx* c, const tsp_schedule* s, void* stream)
 {
     if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
     if (!s) return fail(c, TSP_EINVAL, "schedule is NULL");
-    if (s->ty_cap < 4 || s->ty_cap > 128 || s->items_per_sm < 1 || s->items_per_sm > 64 ||
-        (s->order != 0 && s->order != 1) || s->reserved != 0)
-        return fail(c, TSP_EINVAL,
-                    "schedule: ty_cap in [4,128], items_per_sm in [1,64], order 0 or 1, "
-                    "reserved 0");
+    if (!schedule_valid(*s)) return fail(c, TSP_EINVAL, TSP_SCHEDULE_RANGES);
     if (c->appending)
         return fail(c, TSP_ESTATE, "set_schedule between begin_events and end_events");
     DeviceGuard dg(c->dev);

@@ -98,11 +98,7 @@ int check_index(tsp_batch* b, int i)
 int validate_schedule(tsp_batch* b, const tsp_schedule* s)
 {
     if (!s) return bfail(b, TSP_EINVAL, "schedule is NULL");
-    if (s->ty_cap < 4 || s->ty_cap > 128 || s->items_per_sm < 1 || s->items_per_sm > 64 ||
-        (s->order != 0 && s->order != 1) || s->reserved != 0)
-        return bfail(b, TSP_EINVAL,
-                     "schedule: ty_cap in [4,128], items_per_sm in [1,64], order 0 or 1, "
-                     "reserved 0");
+    if (!schedule_valid(*s)) return bfail(b, TSP_EINVAL, TSP_SCHEDULE_RANGES);
     return TSP_OK;
 }
 

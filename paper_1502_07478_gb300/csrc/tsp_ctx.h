@@ -23,6 +23,14 @@ struct Schedule {
     int order = 0;
 };
 
+// The ranges tsp.h documents for the schedule knobs.
+inline bool schedule_valid(const tsp_schedule& s)
+{
+    return s.ty_cap >= 4 && s.ty_cap <= 128 && s.items_per_sm >= 1 && s.items_per_sm <= 64 &&
+           (s.order == 0 || s.order == 1) && s.reserved == 0;
+}
+#define TSP_SCHEDULE_RANGES "schedule: ty_cap in [4,128], items_per_sm in [1,64], order 0 or 1, reserved 0"
+
 struct tsp_ctx {
     tsp_params p{};
     tsp::Geo g{};

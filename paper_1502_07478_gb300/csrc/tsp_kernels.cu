@@ -345,13 +345,6 @@ __global__ void k_fill(float* p, long long n, float v)
         p[i] = v;
 }
 
-__global__ void k_product(int n, const float* __restrict__ a, const float* __restrict__ b,
-                          float* __restrict__ out)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        out[i] = a[i] * b[i];
-}
-
 __global__ void k_check_image(int n, const float* __restrict__ rho, int* bad)
 {
     int b = 0;
@@ -501,12 +494,6 @@ cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     k_fill<<<blocks_for(n, kAuxThreads * 4, 4096), kAuxThreads, 0, st>>>(p, n, v);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_product(int n, const float* a, const float* b, float* out, cudaStream_t st)
-{
-    k_product<<<blocks_for(n, kAuxThreads * 4, 1024), kAuxThreads, 0, st>>>(n, a, b, out);
     return cudaGetLastError();
 }
 

@@ -105,7 +105,6 @@ cudaError_t launch_thread_pass(const Geo& g, const EventsView& evs, int n, const
 cudaError_t launch_direct_image(const Geo& g, long long n, const float* zu, const float* zd,
                                 const float* dl, unsigned* h, float* out, cudaStream_t st);
 cudaError_t launch_fill(float* p, long long n, float v, cudaStream_t st);
-cudaError_t launch_product(int npix, const float* a, const float* b, float* out, cudaStream_t st);
 cudaError_t launch_check_image(int npix, const float* rho, int* bad, cudaStream_t st);
 
 }  // namespace tsp
