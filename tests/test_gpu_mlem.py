@@ -281,3 +281,46 @@ def test_gamma_cross_term_parity(small):
     assert rel_err(ref, ref0) > 100 * TOL
     Lref = oracle.loglik_grad(st, ev, img, want_rho=False, want_sigma=False)[0]
     assert L == pytest.approx(Lref, rel=1e-6)
+
+
+def test_state_and_argument_errors(small):
+    """Entry points called out of order or with bad arguments return the
+    documented codes and leave the context usable."""
+    from paper_1502_07478_gb300 import TspError
+    from paper_1502_07478_gb300._lib import TSP_EINVAL, TSP_ESTATE
+    w, ev = small
+    r = _recon(w)
+    for call in (lambda: r.direct_image(), lambda: r.iterate(1), lambda: r.loglik(),
+                 lambda: r.autotune()):
+        with pytest.raises(TspError) as ei:
+            call()
+        assert ei.value.code == TSP_ESTATE
+    with pytest.raises(TspError) as ei:
+        r._chk(r._lib.tsp_set_variant(r._h, 7))
+    assert ei.value.code == TSP_EINVAL
+    with pytest.raises(TspError) as ei:                 # 2 gamma^2 >= iz il after the change
+        r2 = _recon(w, gamma=1.5e-3)
+        r2.set_sigma(20.0, 42.0)
+    assert ei.value.code == TSP_EINVAL
+    with pytest.raises(TspError):
+        r.set_schedule(items_per_sm=0)
+    r.upload_events(*ev)
+    r.begin_events(10)
+    r.append_events(*[x[:0] for x in ev])               # empty chunks are accepted
+    r.append_events(*[x[:10] for x in ev])
+    r.end_events()
+    r.iterate(1)
+    assert r.stats()["n_events"] == 10
+    r.close()
+
+
+def test_single_reconstruction_batch_matches_plain(small):
+    from paper_1502_07478_gb300 import Batch
+    w, ev = small
+    b = Batch.from_workloads([w])
+    b.upload_events(0, *ev)
+    b.iterate(4)
+    img = b.read_image(0, out=np.empty((w.ny, w.nz), np.float32))
+    b.close()
+    ref, _ = oracle.mlem(Setup.from_workload(w), ev, 4)
+    assert rel_err(img, ref) <= TOL
