@@ -23,22 +23,27 @@ constexpr int kPadFloats = 128;        // slack after image-sized buffers (>= ma
 
 enum Mode : int { kMlem = 0, kLoglik = 1, kGrad = 2 };
 
-// Threads per persistent block of the passes: for the one-lane-per-row
-// passes as many warps as the register file holds for the lane capacity LMAX
-// (the P cache takes LMAX registers per thread, 65536 registers per SM; some
-// forms spill a few registers there, off the pixel loop, and are still faster
-// than at 512 threads); the two-lanes-per-row passes hold both half-row
-// traversals and stay at 512.  The mode and the batched form do not change
-// the choice.  A group of G <= kMinWarps warps always fits, and a block never
-// has more than 15 groups of two or more warps (one named barrier each, ids
-// 1..15).
+// Threads per persistent block of the passes.  The P cache lives in tensor
+// memory, not registers, so the one-lane-per-row passes (64 registers a
+// thread, a few spilled in some forms, off the pixel loop) run the largest
+// block, 1024 threads, whatever the lane capacity; the two-lanes-per-row passes
+// hold both half-row traversals in registers and run 512 (larger blocks are
+// no faster there).  Mode and batched form do not change the choice.  A group
+// of G <= kMinWarps warps always fits, and a block runs at most 15 groups of
+// two or more warps (one named barrier each, ids 1..15).
 __host__ __device__ constexpr int pass_threads(int lmax, int mode, int nseg, bool batch)
 {
-    return (void)mode, (void)batch,
-           nseg != 1 ? 512 : (lmax <= 12 ? 960 : lmax <= 24 ? 768 : lmax <= 48 ? 640 : 512);
+    return (void)lmax, (void)mode, (void)batch, nseg != 1 ? 512 : 1024;
 }
 constexpr int kMinWarps = 16;
-constexpr int kMaxWarps = 30;
+constexpr int kMaxWarps = 32;
+
+// Event groups of G warps in a block of `warps` warps.  Groups of more than one
+// warp synchronise on named barriers 1..15, so there are at most 15 of them.
+__host__ __device__ constexpr int group_count(int warps, int G)
+{
+    return G > 1 && warps / G > 15 ? 15 : warps / G;
+}
 
 // Per-reconstruction constants, passed by value to the kernels.
 struct Geo {

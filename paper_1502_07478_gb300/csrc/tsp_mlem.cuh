@@ -296,13 +296,94 @@ __device__ __forceinline__ void red_add(const RowK<SMEM>& r, int lim, int m, flo
     }
 }
 
+// P cache in tensor memory.  Each thread keeps the kernel values of its row
+// segment in its own TMEM lane instead of registers: warp w uses lanes
+// 32 (w mod 4) .. +31 (the lane quarter a warp may access) and a slice of
+// tm_slice(LMAX) columns starting at column tm_slice(LMAX) * (w / 4).  Pass 1
+// stores four steps at a time, pass 2 loads them back; the registers this
+// frees go to more resident warps.  (The paper's kernel keeps P in registers
+// or recomputes it.)
+__host__ __device__ constexpr int pow2_at_least(int x, int p = 1)
+{
+    return p >= x ? p : pow2_at_least(x, 2 * p);
+}
+__host__ __device__ constexpr int tm_slice(int lmax) { return pow2_at_least(lmax); }
+// Columns a block of `warps` warps allocates (a power of two, 32 .. 512).
+__host__ __device__ constexpr int tm_block_cols(int lmax, int warps)
+{
+    return pow2_at_least(tm_slice(lmax) * ((warps + 3) / 4) < 32 ? 32
+                                                                 : tm_slice(lmax) * ((warps + 3) / 4));
+}
+
+// Executed by one whole warp; the base address goes to *s_addr.
+template <int NCOLS>
+__device__ __forceinline__ void tm_alloc(unsigned* s_addr)
+{
+    static_assert(NCOLS >= 32 && NCOLS <= 512 && (NCOLS & (NCOLS - 1)) == 0, "TMEM columns");
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(s_addr)),
+                 "n"(NCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+// Executed by the warp that allocated.
+template <int NCOLS>
+__device__ __forceinline__ void tm_dealloc(unsigned base)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "n"(NCOLS)
+                 : "memory");
+}
+
+// Block-wide ordering of tensor-memory operations around a barrier.
+__device__ __forceinline__ void tm_sync_threads()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// TMEM address of this warp's first P column (lane field: its lane quarter).
+template <int LMAX>
+__device__ __forceinline__ unsigned tm_thread_addr(unsigned base, int warp)
+{
+    return base + ((unsigned)(32 * (warp & 3)) << 16) + (unsigned)(tm_slice(LMAX) * (warp >> 2));
+}
+
+__device__ __forceinline__ void tm_st4(unsigned a, float x0, float x1, float x2, float x3)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a),
+                 "f"(x0), "f"(x1), "f"(x2), "f"(x3)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tm_ld4(unsigned a, float& x0, float& x1, float& x2, float& x3)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(x0), "=f"(x1), "=f"(x2), "=f"(x3)
+                 : "r"(a)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tm_wait_st()
+{
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tm_wait_ld()
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // Pass 1, step M (template recursion so that each step's address offset is a
-// compile-time immediate).  P[M] holds the kernel value for M < len (values
-// beyond len are unspecified); Dp the partial denominator; in GRAD mode Ez, El
-// the partial sums of rho' P dlogP/d(iz) and rho' P dlogP/d(il).
-template <int TRAV, int LMAX, bool GRAD, bool SMEM, bool GLD, int M>
+// compile-time immediate).  The kernel value of step M goes to TMEM column
+// tma + M (values beyond the lane's length are unspecified), four steps at a
+// time through P (ST: pass 2 follows); Dp the partial denominator; in GRAD mode Ez, El the partial
+// sums of rho' P dlogP/d(iz) and rho' P dlogP/d(il).
+template <int TRAV, int LMAX, bool GRAD, bool SMEM, bool GLD, bool ST, int M>
 __device__ __forceinline__ void pass1_step(const RowK<SMEM>& r, const RowG& rg, int maxlen,
-                                           float (&P)[LMAX], float& Dp, float& Ez, float& El)
+                                           unsigned tma, float (&P)[4], float& Dp, float& Ez,
+                                           float& El)
 {
     if constexpr (M < LMAX) {
         if constexpr ((M & 3) == 0) {
@@ -317,7 +398,8 @@ __device__ __forceinline__ void pass1_step(const RowK<SMEM>& r, const RowG& rg, 
         const float w = Aw * rq;
         const float arg = fmaf(w, w, fmaf(-su, su, r.C0));
         const float p = rq * ex2_approx(arg);
-        P[M] = p;
+        P[M & 3] = p;
+        if constexpr (ST && (M & 3) == 3) tm_st4(tma + (M - 3), P[0], P[1], P[2], P[3]);
         const int lim = (M & 1) ? r.lim_odd : r.lim_even;
         float rhop;
         if constexpr (GLD)
@@ -343,22 +425,25 @@ __device__ __forceinline__ void pass1_step(const RowK<SMEM>& r, const RowG& rg, 
                 El = fmaf(wgt, dl_, El);
             }
         }
-        pass1_step<TRAV, LMAX, GRAD, SMEM, GLD, M + 1>(r, rg, maxlen, P, Dp, Ez, El);
+        pass1_step<TRAV, LMAX, GRAD, SMEM, GLD, ST, M + 1>(r, rg, maxlen, tma, P, Dp, Ez, El);
     }
 }
 
-// Pass 2, step M: acc[d(M)] += P[M] * invD for M < len.
+// Pass 2, step M: acc[d(M)] += P(M) * invD for M < len, P(M) loaded back from
+// TMEM four steps at a time.
 template <int TRAV, int LMAX, bool SMEM, int M>
-__device__ __forceinline__ void pass2_step(const RowK<SMEM>& r, int maxlen, const float (&P)[LMAX],
-                                           float invD)
+__device__ __forceinline__ void pass2_step(const RowK<SMEM>& r, int maxlen, unsigned tma,
+                                           float (&P)[4], float invD)
 {
     if constexpr (M < LMAX) {
         if constexpr ((M & 3) == 0) {
             if (M >= maxlen) return;
+            tm_ld4(tma + M, P[0], P[1], P[2], P[3]);
+            tm_wait_ld();
         }
         red_add<SMEM, 4 * trav_delta<TRAV>(M)>(r, (M & 1) ? r.lim_odd : r.lim_even, M,
-                                               P[M] * invD);
-        pass2_step<TRAV, LMAX, SMEM, M + 1>(r, maxlen, P, invD);
+                                               P[M & 3] * invD);
+        pass2_step<TRAV, LMAX, SMEM, M + 1>(r, maxlen, tma, P, invD);
     }
 }
 
@@ -371,7 +456,7 @@ template <int TRAV, int LMAX, int MODE, bool SMEM, bool GLD>
 __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, int e, int rowi,
                                            const Frame* f, const float* rp_base, float* acc_base,
                                            int G, int wig, int lane, int bar_id, float* part,
-                                           int& parity, BlockSums* bs)
+                                           int& parity, BlockSums* bs, unsigned tma)
 {
     constexpr bool GRAD = (MODE == kGrad);
     const float4 ev = evs.geo[e];
@@ -381,9 +466,11 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
     make_row<TRAV, LMAX, GRAD, SMEM, GLD>(g, ev, evs.geo64 + e, rws.x + rowi, rowi < rws.y, f,
                                           GLD ? acc_base : rp_base, rp_base, r, rg, bs);
     const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(r.lim_odd, r.lim_even));
-    float P[LMAX];
+    float P[4];
     float Dp = 0.0f, Ez = 0.0f, El = 0.0f;
-    pass1_step<TRAV, LMAX, GRAD, SMEM, GLD, 0>(r, rg, maxlen, P, Dp, Ez, El);
+    pass1_step<TRAV, LMAX, GRAD, SMEM, GLD, MODE != kLoglik, 0>(r, rg, maxlen, tma, P, Dp, Ez,
+                                                                 El);
+    if (MODE != kLoglik) tm_wait_st();
     float D = warp_sum(Dp);
     if (GRAD) {
         Ez = warp_sum(Ez);
@@ -426,7 +513,7 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
             RowK<SMEM> ra = r;
             if (!GLD)
                 ra.base += (decltype(ra.base))((const char*)acc_base - (const char*)rp_base);
-            pass2_step<TRAV, LMAX, SMEM, 0>(ra, maxlen, P, 1.0f / D);
+            pass2_step<TRAV, LMAX, SMEM, 0>(ra, maxlen, tma, P, 1.0f / D);
         }
     }
 }
@@ -438,20 +525,20 @@ template <int LMAX, int MODE, int NSEG, bool SMEM, bool GLD = false>
 __device__ __forceinline__ void process_event(const Geo& g, const EventsView& evs, int e, int G,
                                               int wig, int lane, int bar_id, float* part,
                                               int& parity, const Frame* f, const float* rp_base,
-                                              float* acc_base, BlockSums* bs)
+                                              float* acc_base, BlockSums* bs, unsigned tma)
 {
     if constexpr (NSEG == 1) {
         event_rows<kAlt, LMAX, MODE, SMEM, GLD>(g, evs, e, wig * 32 + lane, f, rp_base, acc_base,
-                                               G, wig, lane, bar_id, part, parity, bs);
+                                               G, wig, lane, bar_id, part, parity, bs, tma);
     } else {
         if ((wig & 1) == 0)
             event_rows<kPos, LMAX, MODE, SMEM, GLD>(g, evs, e, (wig >> 1) * 32 + lane, f,
                                                    rp_base, acc_base, G, wig, lane, bar_id, part,
-                                                   parity, bs);
+                                                   parity, bs, tma);
         else
             event_rows<kNeg, LMAX, MODE, SMEM, GLD>(g, evs, e, (wig >> 1) * 32 + lane, f,
                                                    rp_base, acc_base, G, wig, lane, bar_id, part,
-                                                   parity, bs);
+                                                   parity, bs, tma);
     }
 }
 
@@ -524,9 +611,12 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
     __shared__ Frame s_frame;
     __shared__ BlockSums s_sums;
     __shared__ Inst s_inst;
+    __shared__ unsigned s_tmem;
     const Inst& I = BATCH ? s_inst : p;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kCols = tm_block_cols(LMAX, kWarps);
+    if (warp == 0) tm_alloc<kCols>(&s_tmem);
     init_block_sums(&s_sums);
     if (!BATCH) {
         const int region = p.tl.RH * p.tl.RS;
@@ -540,6 +630,8 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
         }
     }
     int cur = -1;                                 // reconstruction held in s_inst
+    tm_sync_threads();
+    const unsigned tma = tm_thread_addr<LMAX>(s_tmem, warp);
 
     for (;;) {
         if (tid == 0) s_item = atomicAdd(queue, 1);
@@ -571,7 +663,7 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
         const Geo& g = I.g;
         const Tiling& tl = I.tl;
         const int G = I.G;
-        const int ngroups = kWarps / G;
+        const int ngroups = group_count(kWarps, G);
         const int grp = warp / G, wig = warp - grp * G;
         const int region = tl.RH * tl.RS;
         float* s_rp = smem + kPadFloats;
@@ -603,7 +695,8 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
             for (int e = item.y + grp; e < item.y + item.z; e += ngroups)
                 process_event<LMAX, MODE, NSEG, true, GLD>(g, I.evs, e, G, wig, lane, 1 + grp,
                                                            part, parity, &s_frame,
-                                                           GLD ? I.rhop : s_rp, s_acc, &s_sums);
+                                                           GLD ? I.rhop : s_rp, s_acc, &s_sums,
+                                                           tma);
         __syncthreads();
         if (MODE != kLoglik) {
             for (int rr = warp; rr < tl.RH; rr += kWarps) {
@@ -620,8 +713,9 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
             __syncthreads();
         }
     }
-    __syncthreads();
+    tm_sync_threads();
     if (!BATCH || cur >= 0) flush_block_sums(&s_sums, I.accum, MODE);
+    if (warp == 0) tm_dealloc<kCols>(s_tmem);
 }
 
 // Events whose window does not fit their tile's region: same evaluation, with
@@ -635,8 +729,11 @@ k_outliers(Geo g, EventsView evs, int first, int count, const float* __restrict_
     __shared__ float s_part[kWarps * 2 * 3];
     __shared__ Frame s_frame;
     __shared__ BlockSums s_sums;
+    __shared__ unsigned s_tmem;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ngroups = kWarps / G;
+    constexpr int kCols = tm_block_cols(LMAX, kWarps);
+    if (warp == 0) tm_alloc<kCols>(&s_tmem);
+    const int ngroups = group_count(kWarps, G);
     const int grp = warp / G, wig = warp - grp * G;
     float* part = s_part + grp * (2 * 3 * G);
     int parity = 0;
@@ -650,14 +747,16 @@ k_outliers(Geo g, EventsView evs, int first, int count, const float* __restrict_
         s_frame.rw = g.nz;
         s_frame.shear = 0.0f;
     }
-    __syncthreads();
+    tm_sync_threads();
+    const unsigned tma = tm_thread_addr<LMAX>(s_tmem, warp);
     if (grp < ngroups) {
         for (int k = blockIdx.x * ngroups + grp; k < count; k += gridDim.x * ngroups)
             process_event<LMAX, MODE, NSEG, false>(g, evs, first + k, G, wig, lane, 1 + grp, part,
-                                                   parity, &s_frame, rhop, A, &s_sums);
+                                                   parity, &s_frame, rhop, A, &s_sums, tma);
     }
-    __syncthreads();
+    tm_sync_threads();
     flush_block_sums(&s_sums, accum, MODE);
+    if (warp == 0) tm_dealloc<kCols>(s_tmem);
 }
 
 // Batched outlier kernel: items (-1, first, count, reconstruction), one block
@@ -672,7 +771,12 @@ k_outliers_batch(const Inst* __restrict__ table, const int4* __restrict__ items,
     __shared__ Frame s_frame;
     __shared__ BlockSums s_sums;
     __shared__ Inst s_inst;
+    __shared__ unsigned s_tmem;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kCols = tm_block_cols(LMAX, kWarps);
+    if (warp == 0) tm_alloc<kCols>(&s_tmem);
+    tm_sync_threads();
+    const unsigned tma = tm_thread_addr<LMAX>(s_tmem, warp);
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const int4 item = items[it];
         __syncthreads();
@@ -684,7 +788,7 @@ k_outliers_batch(const Inst* __restrict__ table, const int4* __restrict__ items,
         if (tid == 0) s_frame = tile_frame(s_inst.g, s_inst.tl, -1);
         __syncthreads();
         const int G = s_inst.G;
-        const int ngroups = kWarps / G;
+        const int ngroups = group_count(kWarps, G);
         const int grp = warp / G, wig = warp - grp * G;
         float* part = s_part + grp * (2 * 3 * G);
         int parity = 0;
@@ -692,10 +796,12 @@ k_outliers_batch(const Inst* __restrict__ table, const int4* __restrict__ items,
             for (int k = grp; k < item.z; k += ngroups)
                 process_event<LMAX, MODE, NSEG, false>(s_inst.g, s_inst.evs, item.y + k, G, wig,
                                                        lane, 1 + grp, part, parity, &s_frame,
-                                                       s_inst.rhop, s_inst.A, &s_sums);
+                                                       s_inst.rhop, s_inst.A, &s_sums, tma);
         __syncthreads();
         flush_block_sums(&s_sums, s_inst.accum, MODE);
     }
+    tm_sync_threads();
+    if (warp == 0) tm_dealloc<kCols>(s_tmem);
 }
 
 }  // namespace tsp

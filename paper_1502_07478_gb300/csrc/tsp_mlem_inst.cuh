@@ -30,7 +30,7 @@ cudaError_t run_pass(const PassArgs& a, cudaStream_t st)
             p, nullptr, a.items, a.n_items, &a.accum->queue);
     }
     if (a.outlier_count > 0) {
-        const int per_block = pass_threads(LMAX, MODE, NSEG, false) / 32 / a.G;
+        const int per_block = group_count(pass_threads(LMAX, MODE, NSEG, false) / 32, a.G);
         int blocks = (a.outlier_count + per_block - 1) / per_block;
         if (blocks > a.grid) blocks = a.grid;
         k_outliers<LMAX, MODE, NSEG><<<blocks, pass_threads(LMAX, MODE, NSEG, false), 0, st>>>(
