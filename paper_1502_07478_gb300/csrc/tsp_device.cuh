@@ -23,17 +23,16 @@ constexpr int kPadFloats = 128;        // slack after image-sized buffers (>= ma
 
 enum Mode : int { kMlem = 0, kLoglik = 1, kGrad = 2 };
 
-// Threads per persistent block of the passes.  The P cache lives in tensor
-// memory, not registers, so the one-lane-per-row passes (64 registers a
-// thread, a few spilled in some forms, off the pixel loop) run the largest
-// block, 1024 threads, whatever the lane capacity; the two-lanes-per-row passes
-// hold both half-row traversals in registers and run 512 (larger blocks are
-// no faster there).  Mode and batched form do not change the choice.  A group
-// of G <= kMinWarps warps always fits, and a block runs at most 15 groups of
-// two or more warps (one named barrier each, ids 1..15).
+// Threads per persistent block of the passes: 1024 for every pass.  The P
+// cache lives in tensor memory, not registers, so the one-lane-per-row passes
+// fit 64 registers a thread (a few spilled in some forms, off the pixel loop)
+// and the two-lanes-per-row passes hold both half-row traversals without
+// spilling; at 0.5 mm an event takes 16 warps, so a block of 32 runs two events
+// at a time.  A group of G <= kMinWarps warps always fits, and a block runs at
+// most 15 groups of two or more warps (one named barrier each, ids 1..15).
 __host__ __device__ constexpr int pass_threads(int lmax, int mode, int nseg, bool batch)
 {
-    return (void)lmax, (void)mode, (void)batch, nseg != 1 ? 512 : 1024;
+    return (void)lmax, (void)mode, (void)nseg, (void)batch, 1024;
 }
 constexpr int kMinWarps = 16;
 constexpr int kMaxWarps = 32;
