@@ -52,7 +52,7 @@ class Params(C.Structure):
         ("wsigma_z", C.c_double), ("wsigma_dl", C.c_double),
         ("pscale", C.c_double),
         ("a3_printed", C.c_int32), ("form_p", C.c_int32), ("n_threads", C.c_int32),
-        ("pad_", C.c_int32),
+        ("pad_", C.c_int32), ("kappa_z", C.c_double),
     ]
 
 
@@ -81,7 +81,7 @@ def lib():
         _lib.orc_kernel.restype = d
         _lib.orc_kernel_batch.argtypes = [P(Params), C.c_int64, dp, dp, dp, dp, dp, dp, dp]
         _lib.orc_kernel_dlog.argtypes = [P(Params), d, d, d, d, d, dp]
-        _lib.orc_bbox.argtypes = [P(Params), d, dp, dp]
+        _lib.orc_bbox.argtypes = [P(Params), d, d, dp, dp]
         _lib.orc_mlem.argtypes = [P(Params), dp, dp, dp, C.c_int64, dp, dp, C.c_int,
                                   dp, P(Stats)]
         _lib.orc_mlem.restype = C.c_int
@@ -113,6 +113,7 @@ class Setup:
     a3_printed: bool = False
     form_p: bool = False
     n_threads: int = 0
+    kappa_z: float = 0.0
 
     @property
     def dy(self):
@@ -132,7 +133,8 @@ class Setup:
     def params(self) -> Params:
         return Params(self.R, self.L, self.ny, self.nz, self.dy, self.dz, self.sigma_z,
                       self.sigma_dl, self.gamma, self.cut, self.wsigma_z, self.wsigma_dl,
-                      self.pscale, int(self.a3_printed), int(self.form_p), int(self.n_threads), 0)
+                      self.pscale, int(self.a3_printed), int(self.form_p), int(self.n_threads), 0,
+                      self.kappa_z)
 
     def pixel_centres(self):
         yc = -self.R + (np.arange(self.ny) + 0.5) * self.dy
@@ -205,10 +207,11 @@ def kernel_dlog(st: Setup, ey, ez, t, py, pz):
     return out
 
 
-def bbox(st: Setup, t):
+def bbox(st: Setup, t, ez: float = 0.0):
+    """App. B half-extents (hy, hz) of the window of an event at z~ = ez."""
     hy, hz = C.c_double(), C.c_double()
     p = st.params()
-    lib().orc_bbox(C.byref(p), float(t), C.byref(hy), C.byref(hz))
+    lib().orc_bbox(C.byref(p), float(ez), float(t), C.byref(hy), C.byref(hz))
     return hy.value, hz.value
 
 

@@ -44,6 +44,11 @@
  *   R8 Listing 1's rho[l] in the scatter is rho[i]; the listing is Eq. iter-p.
  *   R9 Sensitivity at pixel centres, clamped to >= 0.
  *   R10 Events with D_j = 0 are skipped and counted; then sum_l s_l rho_l = N_used.
+ *   R15 Sec. 3 notes that the z resolution degrades by about 10% from the centre
+ *      of the strips to their ends, without a functional form.  With kappa_z != 0
+ *      an event reconstructed at z~ uses sigma_z (1 + kappa_z min(1, (2 z~/L)^2))
+ *      in its kernel, window and box (kappa_z = 0.1: 10% at the ends); the
+ *      gradient is taken with respect to the base sigma_z.
  */
 #include <math.h>
 #include <stdint.h>
@@ -71,6 +76,7 @@ typedef struct {
     int32_t form_p;    /* 1 = iterate Eq. iter-p on rho' (no s); 0 = Eq. iter */
     int32_t n_threads; /* OpenMP threads; <= 0 = library default */
     int32_t pad_;
+    double kappa_z;    /* z dependence of sigma_z (reading R15); 0 = constant */
 } orc_params;
 
 typedef struct {
@@ -125,6 +131,15 @@ void orc_sensitivity(const orc_params* p, double* s)
 }
 
 /* ------------------------------------------------------- correlation matrix */
+
+/* Reading R15: the factor on sigma_z for an event reconstructed at z~ = ez. */
+static double zfactor(const orc_params* p, double ez)
+{
+    double s = 2.0 * ez / p->L;
+    s = s * s;
+    if (s > 1.0) s = 1.0;
+    return 1.0 + p->kappa_z * s;
+}
 
 /* C^-1 of Sec. 3 for the given sigmas (general form with the cross term gamma). */
 static void cinv_matrix(double sz, double sdl, double g, double C[3][3])
@@ -193,7 +208,7 @@ static double window_bq(const orc_params* p, double ey, double ez, double t,
                         double py, double pz)
 {
     double C[3][3], o[3], a[3], b[3];
-    double wz = p->wsigma_z > 0 ? p->wsigma_z : p->sigma_z;
+    double wz = (p->wsigma_z > 0 ? p->wsigma_z : p->sigma_z) * zfactor(p, ez);
     double wl = p->wsigma_dl > 0 ? p->wsigma_dl : p->sigma_dl;
     cinv_matrix(wz, wl, p->gamma, C);
     oab_vectors(p, ey, ez, t, py, pz, o, a, b);
@@ -205,7 +220,7 @@ static double kernel_value(const orc_params* p, double ey, double ez, double t,
                            double py, double pz, int* qbad)
 {
     double C[3][3], o[3], a[3], b[3];
-    cinv_matrix(p->sigma_z, p->sigma_dl, p->gamma, C);
+    cinv_matrix(p->sigma_z * zfactor(p, ez), p->sigma_dl, p->gamma, C);
     oab_vectors(p, ey, ez, t, py, pz, o, a, b);
     double aCa = quad(a, C, a), oCb = quad(o, C, b), bCb = quad(b, C, b), aCb = quad(a, C, b);
     double Q = aCa + 2.0 * oCb;
@@ -219,22 +234,25 @@ static double kernel_value(const orc_params* p, double ey, double ez, double t,
 }
 
 /* d log P / d sigma_z and d log P / d sigma_dl at fixed window (reading R4),
- * from log P = 1/2 log det C^-1 - 1/2 log Q - 1/2 bC^-1b + 1/2 (aC^-1b)^2/Q + const. */
+ * from log P = 1/2 log det C^-1 - 1/2 log Q - 1/2 bC^-1b + 1/2 (aC^-1b)^2/Q + const.
+ * sigma_z is the base value: the event's own sigma_z is f sigma_z (reading R15),
+ * so d(C^-1)_zz / d sigma_z = -2 f / (f sigma_z)^3. */
 static void kernel_dlog(const orc_params* p, double ey, double ez, double t,
                         double py, double pz, double dlog[2])
 {
     double C[3][3], Ci[3][3], o[3], a[3], b[3];   /* C holds C^-1 */
-    cinv_matrix(p->sigma_z, p->sigma_dl, p->gamma, C);
+    double f = zfactor(p, ez);
+    cinv_matrix(p->sigma_z * f, p->sigma_dl, p->gamma, C);
     inv3(C, Ci);
     oab_vectors(p, ey, ez, t, py, pz, o, a, b);
     double aCa = quad(a, C, a), oCb = quad(o, C, b), bCb = quad(b, C, b), aCb = quad(a, C, b);
     double Q = aCa + 2.0 * oCb;
     (void)bCb;
-    double sz = p->sigma_z, sl = p->sigma_dl;
+    double sz = p->sigma_z * f, sl = p->sigma_dl;
     for (int k = 0; k < 2; ++k) {
         double dC[3][3];
         memset(dC, 0, sizeof dC);
-        if (k == 0) { dC[0][0] = dC[1][1] = -2.0 / (sz * sz * sz); }
+        if (k == 0) { dC[0][0] = dC[1][1] = -2.0 * f / (sz * sz * sz); }
         else        { dC[2][2] = -2.0 / (sl * sl * sl); }
         /* d log det(C^-1) = tr(C d(C^-1)); Ci holds C, the inverse of C^-1 */
         double tr = 0.0;
@@ -274,10 +292,11 @@ void orc_kernel_dlog(const orc_params* p, double ey, double ez, double t,
     kernel_dlog(p, ey, ez, t, py, pz, dlog2);
 }
 
-/* App. B (reading R7): half-extents of the bounding box of the cut ellipse. */
-void orc_bbox(const orc_params* p, double t, double* hy, double* hz)
+/* App. B (reading R7): half-extents of the bounding box of the cut ellipse of an
+ * event at z~ = ez (which sets its sigma_z, reading R15). */
+void orc_bbox(const orc_params* p, double ez, double t, double* hy, double* hz)
 {
-    double wz = p->wsigma_z > 0 ? p->wsigma_z : p->sigma_z;
+    double wz = (p->wsigma_z > 0 ? p->wsigma_z : p->sigma_z) * zfactor(p, ez);
     double wl = p->wsigma_dl > 0 ? p->wsigma_dl : p->sigma_dl;
     double c2 = 1.0 / (1.0 + t * t), s2 = 1.0 - c2;
     *hy = p->cut * wl * sqrt(c2) / 2.0;
@@ -310,7 +329,7 @@ static int64_t event_window(const orc_params* p, double zu, double zd, double dl
     orc_direct(p, zu, zd, dl, &ey, &ez, &t);
     *ey_o = ey; *ez_o = ez; *t_o = t;
     double hy, hz;
-    orc_bbox(p, t, &hy, &hz);
+    orc_bbox(p, ez, t, &hy, &hz);
     double y0 = -p->R + 0.5 * p->dy, z0 = -0.5 * p->L + 0.5 * p->dz;
     double fy_lo = floor((ey - hy - y0) / p->dy) - 1, fy_hi = ceil((ey + hy - y0) / p->dy) + 1;
     double fz_lo = floor((ez - hz - z0) / p->dz) - 1, fz_hi = ceil((ez + hz - z0) / p->dz) + 1;
