@@ -45,7 +45,7 @@ MUFU_PER_SM_CLK = 16        # SFU results per SM per clock (sm_100-class)
 # DRAM bytes per event of one MLEM tile pass (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch over 1e6 events of the 1 mm workload,
 # profiles/k_tiles_paper_1mm_1e6.md); the traffic grows with the events.
-TILE_PASS_DRAM_B_PER_EVENT = 47.9
+TILE_PASS_DRAM_B_PER_EVENT = 47.8
 
 
 def _peaks():

@@ -60,7 +60,13 @@ typedef struct {
     int32_t reserved;
     double gamma;      /* cross term of C^-1 between z_u (z_d) and delta_l (Sec. 3):
                           C^-1 = [[1/sz^2, 0, g], [0, 1/sz^2, -g], [g, -g, 1/sdl^2]];
-                          0 = diagonal; finite with 2 g^2 < 1/(sz^2 sdl^2) */
+                          0 = diagonal; finite with 2 g^2 < 1/(sz^2 sdl^2 (1+kappa_z)^2) */
+    double kappa_z;    /* z dependence of the z resolution (Sec. 3 notes about 10%
+                          from the strip centre to its ends, without a form): an
+                          event reconstructed at z~ uses
+                          sz (1 + kappa_z min(1, (2 z~/L)^2)) in its kernel, window
+                          and box; in [0, 1]; 0 = constant sz.  Gradients are with
+                          respect to the base sigma_z. */
 } tsp_params;
 
 /* Counters of the last upload / pass (filled by tsp_stats). */

@@ -31,7 +31,7 @@ class Params(C.Structure):
     _fields_ = [("R", C.c_double), ("L", C.c_double), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("dy", C.c_double), ("dz", C.c_double), ("sigma_z", C.c_double),
                 ("sigma_dl", C.c_double), ("cut", C.c_double), ("flags", C.c_int32),
-                ("reserved", C.c_int32), ("gamma", C.c_double)]
+                ("reserved", C.c_int32), ("gamma", C.c_double), ("kappa_z", C.c_double)]
 
 
 class Stats(C.Structure):

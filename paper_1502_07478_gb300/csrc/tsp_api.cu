@@ -79,8 +79,10 @@ int plan(tsp_ctx* c)
     const double cut = p.cut > 0 ? p.cut : 3.0;
     c->g = make_geo(p);
 
-    // lane capacity: the longest chord of the ellipse is 2 cut sigma_z / sqrt(2)
-    const double umax = cut * p.sigma_z / std::sqrt(2.0);
+    // lane capacity: the longest chord of the ellipse is 2 cut sigma_z / sqrt(2),
+    // with the largest sigma_z of any event, sigma_z (1 + kappa_z)
+    const double szmax = p.sigma_z * (1.0 + p.kappa_z);
+    const double umax = cut * szmax / std::sqrt(2.0);
     const int need = (int)std::floor(2.0 * umax / dz) + 2;
     // one lane per row (whole chord), or two lanes per row (one per half)
     int best_l = 0, best_s = 0;
@@ -110,7 +112,7 @@ int plan(tsp_ctx* c)
     // (sqrt(2) sigma_z / 2R); events outside go to the outlier path.
     Tiling& tl = c->tl;
     const double dtb = 1.0 / 16.0;
-    const double t_max = p.L / (2.0 * p.R) + 6.0 * std::sqrt(2.0) * p.sigma_z / (2.0 * p.R);
+    const double t_max = p.L / (2.0 * p.R) + 6.0 * std::sqrt(2.0) * szmax / (2.0 * p.R);
     tl.nb = (int)std::ceil(2.0 * t_max / dtb);
     tl.dtb = (float)dtb;
     tl.inv_dtb = (float)(1.0 / dtb);
@@ -199,7 +201,9 @@ int validate(const tsp_params* p, tsp_ctx* c)
     if (!(p->cut == 0.0 || pos(p->cut))) return fail(c, TSP_EINVAL, "cut must be 0 or > 0");
     if (p->flags != 0) return fail(c, TSP_EINVAL, "flags must be 0");
     if (!cinv_valid(*p))
-        return fail(c, TSP_EINVAL, "gamma must be finite with 2 gamma^2 < 1/(sigma_z^2 sigma_dl^2)");
+        return fail(c, TSP_EINVAL,
+                    "kappa_z must be in [0, 1] and gamma finite with "
+                    "2 gamma^2 < 1/((sigma_z (1 + kappa_z))^2 sigma_dl^2)");
     return TSP_OK;
 }
 

@@ -62,11 +62,65 @@ struct Geo {
     // the cross term gamma of C^-1 (Sec. 3) enters only row constants:
     //   Q += -gR8 t c2i sec (y + Dy),  aCb += -gR4 c2i sec Dy  (bCb unchanged)
     float gR8, gR4;         // 8 gamma R, 4 gamma R
+    float g2;               // 2 gamma^2
     float ldz, ldl;         // (1/2) d log det(C^-1) / d iz, / d il
+    // z-dependent resolution (Sec. 3): an event at z~ has sigma_z f,
+    // f = 1 + kz min(1, zs2 z~^2); kz = 0 keeps sigma_z constant
+    float kz, zs2;          // kappa_z, (2/L)^2
     // double-precision copies for the exact window decision near its boundary
     double y0d, z0d, dyd, dzd, Rd, izd, ild, cut2d;
     double Ld;              // strip length
+    double kzd, zs2d;
 };
+
+// Resolution constants of one event.  With kz = 0 they are the Geo's; else the
+// event's sigma_z is sigma_z f (f = 1 + kz min(1, (2 z~/L)^2)), so that
+// iz -> iz/f^2, 1/sqrt(2 iz) -> f/sqrt(2 iz), sqrt(log2(e) iz) -> /f, the box
+// term hz_a -> hz_a f^2, log2 K moves by half the log2 of the ratio of
+// det(C^-1) = iz (iz il - 2 gamma^2), and so do the log-determinant
+// derivatives.  inv_f2 = 1/f^2 = d iz_event / d iz turns the event's d/d iz
+// into one with respect to the base value.  The quantities that decide window
+// membership are formed with explicitly rounded operations, so that the event
+// preparation and the passes derive the same chords.
+struct EvSig {
+    float iz, inv_sqrt_2iz, ksu, log2K, hz_a, ldz, ldl, inv_f, inv_f2;
+};
+
+// The context's constants (kz = 0).
+__device__ __forceinline__ EvSig geo_sig(const Geo& g)
+{
+    EvSig s;
+    s.iz = g.iz;
+    s.inv_sqrt_2iz = g.inv_sqrt_2iz;
+    s.ksu = g.ksu;
+    s.log2K = g.log2K;
+    s.hz_a = g.hz_a;
+    s.ldz = g.ldz;
+    s.ldl = g.ldl;
+    s.inv_f = 1.0f;
+    s.inv_f2 = 1.0f;
+    return s;
+}
+
+__device__ __forceinline__ EvSig ev_sig(const Geo& g, const float4& ev)
+{
+    if (g.kz == 0.0f) return geo_sig(g);
+    EvSig s;
+    const float f = __fmaf_rn(g.kz, fminf(__fmul_rn(__fmul_rn(ev.y, ev.y), g.zs2), 1.0f), 1.0f);
+    const float f2 = __fmul_rn(f, f);
+    s.inv_f = __fdiv_rn(1.0f, f);
+    s.inv_f2 = __fdiv_rn(1.0f, f2);
+    s.iz = __fmul_rn(g.iz, s.inv_f2);
+    s.inv_sqrt_2iz = __fmul_rn(g.inv_sqrt_2iz, f);
+    s.ksu = __fdiv_rn(g.ksu, f);
+    s.hz_a = __fmul_rn(g.hz_a, f2);
+    // det(C^-1) = iz (iz il - 2 gamma^2), base (e0) and event (e1) factors
+    const float e0 = g.iz * g.il - g.g2, e1 = s.iz * g.il - g.g2;
+    s.log2K = g.log2K + 0.5f * log2f(s.inv_f2 * (e1 / e0));
+    s.ldz = (s.iz * g.il - 0.5f * g.g2) / (s.iz * e1);
+    s.ldl = 0.5f * s.iz / e1;
+    return s;
+}
 
 // Image tiling used by the shared-memory accumulation.
 //
@@ -252,10 +306,19 @@ constexpr float kRemRel = 1e-5f;
 
 // bCb of column iz in the row with offset Dy (B0 = 4 il Dy^2 c2i), double
 // precision: the window quantity of Sec. 3 for a diagonal C^-1.
-__device__ __forceinline__ double bq_fp64(const Geo& g, const Ev64& e, double Dy, double B0, int iz)
+// The event's iz in double precision (see EvSig).
+__device__ __forceinline__ double ev_izd(const Geo& g, const Ev64& e)
+{
+    if (g.kzd == 0.0) return g.izd;
+    const double f = 1.0 + g.kzd * fmin(e.y * e.y * g.zs2d, 1.0);
+    return g.izd / (f * f);
+}
+
+__device__ __forceinline__ double bq_fp64(const Geo& g, const Ev64& e, double izd, double Dy,
+                                          double B0, int iz)
 {
     const double u = (g.z0d + (double)iz * g.dzd) - (e.y + e.z * Dy);
-    return 2.0 * g.izd * u * u + B0;
+    return 2.0 * izd * u * u + B0;
 }
 
 __device__ __forceinline__ int float_to_index(float x)
@@ -266,7 +329,7 @@ __device__ __forceinline__ int float_to_index(float x)
 // Explicitly rounded operations (never contracted into FMAs), so that the
 // event preparation and the MLEM passes derive bit-identical chords whatever
 // the surrounding code lets the compiler fuse.
-__device__ __forceinline__ Chord row_chord(const Geo& g, const float4& ev,
+__device__ __forceinline__ Chord row_chord(const Geo& g, const EvSig& es, const float4& ev,
                                            const Ev64* __restrict__ ev64, int iy)
 {
     Chord c;
@@ -283,12 +346,12 @@ __device__ __forceinline__ Chord row_chord(const Geo& g, const float4& ev,
     if (rem >= 0.0f) {
         const float rs = rsqrt_approx(fmaxf(rem, 1e-30f));   // 1/sqrt(rem)
         const float sr = __fmul_rn(rem, rs);                  // sqrt(rem)
-        const float umax = __fmul_rn(sr, g.inv_sqrt_2iz);
+        const float umax = __fmul_rn(sr, es.inv_sqrt_2iz);
         const float xlo = __fmul_rn(__fsub_rn(__fsub_rn(c.zc, umax), g.z0), g.inv_dz);
         const float xhi = __fmul_rn(__fsub_rn(__fadd_rn(c.zc, umax), g.z0), g.inv_dz);
         const float coord = (fabsf(c.zc) + umax + fabsf(g.z0)) * g.inv_dz;
         const float m = kEndRel * (fabsf(xhi) + coord) +
-                        kEndRel * g.cut2 * g.inv_sqrt_2iz * g.inv_dz * rs;
+                        kEndRel * g.cut2 * es.inv_sqrt_2iz * g.inv_dz * rs;
         unsure_lo = fabsf(xlo - rintf(xlo)) < m;
         unsure_hi = fabsf(xhi - rintf(xhi)) < m;
         a = float_to_index(ceilf(xlo));
@@ -296,6 +359,8 @@ __device__ __forceinline__ Chord row_chord(const Geo& g, const float4& ev,
     }
     if (unsure_rem || unsure_lo || unsure_hi) {
         const Ev64 e = *ev64;
+        // (with the context's constants inv_f2 is the literal 1: no z profile)
+        const double izd = es.inv_f2 == 1.0f ? g.izd : ev_izd(g, e);
         const double Dy = (g.y0d + (double)iy * g.dyd) - e.x;
         const double B0 = 4.0 * g.ild * Dy * Dy * e.w;
         if (unsure_rem) {
@@ -304,19 +369,19 @@ __device__ __forceinline__ Chord row_chord(const Geo& g, const float4& ev,
             a = 0;
             b = -1;
             for (int iz = k - 2; iz <= k + 2; ++iz) {
-                if (bq_fp64(g, e, Dy, B0, iz) <= g.cut2d) {
+                if (bq_fp64(g, e, izd, Dy, B0, iz) <= g.cut2d) {
                     if (b < a) a = iz;
                     b = iz;
                 }
             }
         } else {
             if (unsure_lo) {
-                if (bq_fp64(g, e, Dy, B0, a - 1) <= g.cut2d) --a;
-                else if (bq_fp64(g, e, Dy, B0, a) > g.cut2d) ++a;
+                if (bq_fp64(g, e, izd, Dy, B0, a - 1) <= g.cut2d) --a;
+                else if (bq_fp64(g, e, izd, Dy, B0, a) > g.cut2d) ++a;
             }
             if (unsure_hi) {
-                if (bq_fp64(g, e, Dy, B0, b + 1) <= g.cut2d) ++b;
-                else if (bq_fp64(g, e, Dy, B0, b) > g.cut2d) --b;
+                if (bq_fp64(g, e, izd, Dy, B0, b + 1) <= g.cut2d) ++b;
+                else if (bq_fp64(g, e, izd, Dy, B0, b) > g.cut2d) --b;
             }
         }
     }
@@ -331,21 +396,21 @@ __device__ __forceinline__ Chord row_chord(const Geo& g, const float4& ev,
 
 // Row polynomials of Eq. kernel along the chord of row c (u = z - zc):
 //   Q(u) = aCa + 2 oCb = Qc + gam2 u,    aCb(u) = alpha u + beta.
-__device__ __forceinline__ void row_q(const Geo& g, const float4& ev, const Chord& c, float& Qc,
-                                      float& gam2)
+__device__ __forceinline__ void row_q(const Geo& g, const EvSig& es, const float4& ev,
+                                      const Chord& c, float& Qc, float& gam2)
 {
     const float t = ev.z, c2i = ev.w, y = c.y, Dy = c.Dy, y2 = y * y;
-    const float aCa = 2.0f * g.iz * (g.R * g.R + y2) * c2i * c2i + 4.0f * g.il * y2 * t * t * c2i;
+    const float aCa = 2.0f * es.iz * (g.R * g.R + y2) * c2i * c2i + 4.0f * g.il * y2 * t * t * c2i;
     Qc = aCa + 4.0f * g.il * y * fmaf(2.0f * t, t, 1.0f) * Dy * c2i;   // Q at u = 0
     if (g.gR8 != 0.0f) Qc -= g.gR8 * t * c2i * sqrtf(c2i) * (y + Dy);
-    gam2 = -4.0f * g.iz * y * t * c2i;                                 // 2 oCb slope
+    gam2 = -4.0f * es.iz * y * t * c2i;                                // 2 oCb slope
 }
 
-__device__ __forceinline__ void row_acb(const Geo& g, const float4& ev, const Chord& c,
-                                        float& alpha, float& beta)
+__device__ __forceinline__ void row_acb(const Geo& g, const EvSig& es, const float4& ev,
+                                        const Chord& c, float& alpha, float& beta)
 {
     const float t = ev.z, c2i = ev.w, y = c.y, Dy = c.Dy;
-    alpha = -2.0f * g.iz * y * c2i;            // aCb slope in u
+    alpha = -2.0f * es.iz * y * c2i;           // aCb slope in u
     beta = 4.0f * g.il * y * t * Dy * c2i;     // aCb at u = 0
     if (g.gR4 != 0.0f) beta -= g.gR4 * c2i * sqrtf(c2i) * Dy;
 }
@@ -353,12 +418,13 @@ __device__ __forceinline__ void row_acb(const Geo& g, const float4& ev, const Ch
 // Bounding box of the event's window in pixel rows and columns, clipped to the
 // grid (App. B half-extents, widened by 1e-5 relative so that FP32 rounding
 // never drops a row whose chord is non-empty).
-__device__ __forceinline__ void event_bbox(const Geo& g, const float4& ev, int& iy_lo, int& nrows,
+__device__ __forceinline__ void event_bbox(const Geo& g, const EvSig& es, const float4& ev,
+                                           int& iy_lo, int& nrows,
                                            int& iz_lo, int& ncols)
 {
     float hy = g.hy_coef * rsqrtf(ev.w) * 1.00001f;
     float s2 = ev.z * ev.z / ev.w;
-    float hz = sqrtf(fmaf(g.hz_b, s2, g.hz_a)) * 1.00001f;
+    float hz = sqrtf(fmaf(g.hz_b, s2, es.hz_a)) * 1.00001f;
     nrows = clamp_range(ceilf((ev.x - hy - g.y0) * g.inv_dy), floorf((ev.x + hy - g.y0) * g.inv_dy),
                         g.ny, iy_lo);
     ncols = clamp_range(ceilf((ev.y - hz - g.z0) * g.inv_dz), floorf((ev.y + hz - g.z0) * g.inv_dz),

@@ -81,8 +81,9 @@ __global__ void k_setup(Geo g, Tiling tl, long long n, const float* __restrict__
             ++bad;
         } else {
             ev = make_float4((float)e64.x, (float)e64.y, (float)e64.z, (float)e64.w);
+            const EvSig es = ev_sig(g, ev);
             int iy_lo, nrows, iz_lo, ncols;
-            event_bbox(g, ev, iy_lo, nrows, iz_lo, ncols);
+            event_bbox(g, es, ev, iy_lo, nrows, iz_lo, ncols);
             // angle bin and sheared tile of the pixel holding the window centre
             const float fb = floorf((ev.z - tl.t0) * tl.inv_dtb);
             const bool bin_ok = fb >= 0.0f && fb < (float)tl.nb;
@@ -101,7 +102,7 @@ __global__ void k_setup(Geo g, Tiling tl, long long n, const float* __restrict__
             unsigned long long cnt = 0;
             for (int r = 0; r < nrows; ++r) {
                 const int iy = iy_lo + r;
-                const Chord c = row_chord(g, ev, &e64, iy);
+                const Chord c = row_chord(g, es, ev, &e64, iy);
                 if (c.count > 0) {
                     if (first < 0) first = iy;
                     last = iy;
@@ -359,7 +360,11 @@ __global__ void k_check_image(int n, const float* __restrict__ rho, int* bad)
 
 bool cinv_valid(const tsp_params& p)
 {
-    const double iz = 1.0 / (p.sigma_z * p.sigma_z), il = 1.0 / (p.sigma_dl * p.sigma_dl);
+    // kappa_z in [0, 1]; C^-1 positive definite for every event's sigma_z,
+    // the largest being sigma_z (1 + kappa_z)
+    if (!(std::isfinite(p.kappa_z) && p.kappa_z >= 0.0 && p.kappa_z <= 1.0)) return false;
+    const double szmax = p.sigma_z * (1.0 + p.kappa_z);
+    const double iz = 1.0 / (szmax * szmax), il = 1.0 / (p.sigma_dl * p.sigma_dl);
     return std::isfinite(p.gamma) && 2.0 * p.gamma * p.gamma < iz * il;
 }
 
@@ -396,6 +401,11 @@ Geo make_geo(const tsp_params& p)
     g.inv_sqrt_2iz = (float)(1.0 / std::sqrt(2.0 * iz));
     g.gR8 = (float)(8.0 * gm * p.R);
     g.gR4 = (float)(4.0 * gm * p.R);
+    g.g2 = (float)(2.0 * gm * gm);
+    g.kz = (float)p.kappa_z;
+    g.zs2 = (float)(4.0 / (p.L * p.L));
+    g.kzd = p.kappa_z;
+    g.zs2d = 4.0 / (p.L * p.L);
     g.ldz = (float)((iz * il - gm * gm) / (iz * (iz * il - 2.0 * gm * gm)));
     g.ldl = (float)(0.5 * iz / (iz * il - 2.0 * gm * gm));
     g.y0d = -p.R + 0.5 * dy;

@@ -113,8 +113,8 @@ __device__ __forceinline__ void row_idle(RowK<SMEM>& r, RowG& rg)
 // the clamp keeps every access in bounds regardless (clipped pixels are
 // counted).
 template <int TRAV, int LMAX, bool GRAD, bool SMEM, bool GLD>
-__device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const Ev64* ev64,
-                                         int iy, bool valid_row, const Frame* fp,
+__device__ __forceinline__ void make_row(const Geo& g, const EvSig& es, const float4& ev,
+                                         const Ev64* ev64, int iy, bool valid_row, const Frame* fp,
                                          const float* base, const float* gimg, RowK<SMEM>& r,
                                          RowG& rg, BlockSums* bs)
 {
@@ -125,7 +125,7 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const E
     const Frame f = *fp;
     float Qc = 0.0f, gam2 = 0.0f;
     if (valid_row) {
-        c = row_chord(g, ev, ev64, iy);
+        c = row_chord(g, es, ev, ev64, iy);
         lo = c.lo;
         hi = c.lo + c.count - 1;
         if (c.count > 0 && (iy < f.oy || iy >= f.oy + f.rh)) {
@@ -140,7 +140,7 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const E
             hi = hi2;
         }
         if (hi >= lo) {
-            row_q(g, ev, c, Qc, gam2);
+            row_q(g, es, ev, c, Qc, gam2);
             // Reading R5: P = 0 where Q <= 0.  Q is linear along the chord, so
             // the pixels with Q > 0 form a sub-range; keep only that.
             const float ulo = fmaf((float)lo, g.dz, g.z0) - c.zc;
@@ -191,7 +191,7 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const E
     }
     const float t = ev.z, c2i = ev.w, y = c.y, Dy = c.Dy;
     float alpha, beta;
-    row_acb(g, ev, c, alpha, beta);
+    row_acb(g, es, ev, c, alpha, beta);
     const float u0 = fmaf((float)o, g.dz, g.z0) - c.zc;
     const int sidx = (iy - f.oy) * f.stride + (o - z0row);
     if constexpr (SMEM)
@@ -203,9 +203,9 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const E
     r.dQ = gam2 * g.dz;
     r.A0 = g.kA * fmaf(alpha, u0, beta);
     r.dA = g.kA * alpha * g.dz;
-    r.su0 = g.ksu * u0;
-    r.dsu = g.ksu * g.dz;
-    r.C0 = g.log2K - g.half_log2e * c.B0;
+    r.su0 = es.ksu * u0;
+    r.dsu = es.ksu * g.dz;
+    r.C0 = es.log2K - g.half_log2e * c.B0;
     if (GRAD) {
         const float y2 = y * y;
         rg.u0 = u0;
@@ -222,10 +222,20 @@ __device__ __forceinline__ void make_row(const Geo& g, const float4& ev, const E
         rg.cz0 = -2.0f * y * c2i * u0;
         rg.dcz = -2.0f * y * c2i * g.dz;
         const float Bl = 4.0f * Dy * Dy * c2i;
-        rg.kz = g.ldz;
-        rg.kl = g.ldl - 0.5f * Bl;
+        rg.kz = es.ldz;
+        rg.kl = es.ldl - 0.5f * Bl;
         rg.cl = 4.0f * y * t * Dy * c2i;
         rg.qlh = 2.0f * y2 * t * t * c2i + 2.0f * y * fmaf(2.0f * t, t, 1.0f) * Dy * c2i;
+        // the sum Ez is wanted with respect to the base iz: d/d iz = (1/f^2) d/d iz_event,
+        // so every term of the z derivative carries 1/f^2 (u through 1/f, as it
+        // enters squared); with a constant sigma_z these factors are 1
+        rg.u0 *= es.inv_f;
+        rg.du *= es.inv_f;
+        rg.qz0 *= es.inv_f2;
+        rg.dqz *= es.inv_f2;
+        rg.cz0 *= es.inv_f2;
+        rg.dcz *= es.inv_f2;
+        rg.kz *= es.inv_f2;
     }
 }
 
@@ -452,7 +462,7 @@ __device__ __forceinline__ void pass2_step(const RowK<SMEM>& r, int maxlen, unsi
 // cross-warp reduction (double-buffered by parity).
 // GLD (tiles that stage only A): rho' is read from the global image rp_base
 // and the frame addresses the staged accumulator acc_base.
-template <int TRAV, int LMAX, int MODE, bool SMEM, bool GLD>
+template <int TRAV, int LMAX, int MODE, bool SMEM, bool GLD, bool KZ>
 __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, int e, int rowi,
                                            const Frame* f, const float* rp_base, float* acc_base,
                                            int G, int wig, int lane, int bar_id, float* part,
@@ -472,7 +482,9 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
         const int mid = (rws.y - 1) >> 1, k = rowi >> 1;
         ri = (rowi & 1) ? mid + k + 1 : mid - k;
     }
-    make_row<TRAV, LMAX, GRAD, SMEM, GLD>(g, ev, evs.geo64 + e, rws.x + ri, ri >= 0 && ri < rws.y, f,
+    // KZ: the event's own sigma_z (z profile); else the context's constants
+    make_row<TRAV, LMAX, GRAD, SMEM, GLD>(g, KZ ? ev_sig(g, ev) : geo_sig(g), ev, evs.geo64 + e,
+                                          rws.x + ri, ri >= 0 && ri < rws.y, f,
                                           GLD ? acc_base : rp_base, rp_base, r, rg, bs);
     const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(r.lim_odd, r.lim_even));
     float P[4];
@@ -530,22 +542,22 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
 // NSEG = 1: lane-row q = wig*32 + lane covers its row whole (kAlt).  NSEG = 2:
 // even warps cover the right halves and odd warps the left halves of rows
 // (wig/2)*32 + lane (a warp-uniform choice, no divergence).
-template <int LMAX, int MODE, int NSEG, bool SMEM, bool GLD = false>
+template <int LMAX, int MODE, int NSEG, bool SMEM, bool GLD, bool KZ>
 __device__ __forceinline__ void process_event(const Geo& g, const EventsView& evs, int e, int G,
                                               int wig, int lane, int bar_id, float* part,
                                               int& parity, const Frame* f, const float* rp_base,
                                               float* acc_base, BlockSums* bs, unsigned tma)
 {
     if constexpr (NSEG == 1) {
-        event_rows<kAlt, LMAX, MODE, SMEM, GLD>(g, evs, e, wig * 32 + lane, f, rp_base, acc_base,
+        event_rows<kAlt, LMAX, MODE, SMEM, GLD, KZ>(g, evs, e, wig * 32 + lane, f, rp_base, acc_base,
                                                G, wig, lane, bar_id, part, parity, bs, tma);
     } else {
         if ((wig & 1) == 0)
-            event_rows<kPos, LMAX, MODE, SMEM, GLD>(g, evs, e, (wig >> 1) * 32 + lane, f,
+            event_rows<kPos, LMAX, MODE, SMEM, GLD, KZ>(g, evs, e, (wig >> 1) * 32 + lane, f,
                                                    rp_base, acc_base, G, wig, lane, bar_id, part,
                                                    parity, bs, tma);
         else
-            event_rows<kNeg, LMAX, MODE, SMEM, GLD>(g, evs, e, (wig >> 1) * 32 + lane, f,
+            event_rows<kNeg, LMAX, MODE, SMEM, GLD, KZ>(g, evs, e, (wig >> 1) * 32 + lane, f,
                                                    rp_base, acc_base, G, wig, lane, bar_id, part,
                                                    parity, bs, tma);
     }
@@ -606,8 +618,13 @@ __device__ __forceinline__ Frame tile_frame(const Geo& g, const Tiling& tl, int 
 // `p`.  Batched form: item.w indexes `table`, whose record is copied to shared
 // memory when it changes.  `queue` is the work counter (zero at launch).
 // GLD: only the accumulator is staged (windows too large for both regions);
-// rho' is read from the global image through the read-only cache.
-template <int LMAX, int MODE, int NSEG, bool BATCH, bool GLD = false>
+// rho' is read from the global image through the read-only cache.  KZ: the
+// plain form for a z-dependent sigma_z (each event's own resolution
+// constants); the plain form without it reads the context's constants, and
+// the batched form takes each event's, whatever its reconstruction's profile.
+// (The two plain forms are separate kernels because the gradient pass is at
+// the register limit: holding both row setups in one kernel spilled there.)
+template <int LMAX, int MODE, int NSEG, bool BATCH, bool GLD = false, bool KZ = false>
 __global__ void __launch_bounds__(pass_threads(LMAX, MODE, NSEG, BATCH), 1)
 k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, int n_items,
         int* queue)
@@ -702,10 +719,9 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
         __syncthreads();
         if (grp < ngroups)
             for (int e = item.y + grp; e < item.y + item.z; e += ngroups)
-                process_event<LMAX, MODE, NSEG, true, GLD>(g, I.evs, e, G, wig, lane, 1 + grp,
-                                                           part, parity, &s_frame,
-                                                           GLD ? I.rhop : s_rp, s_acc, &s_sums,
-                                                           tma);
+                process_event<LMAX, MODE, NSEG, true, GLD, BATCH || KZ>(
+                    g, I.evs, e, G, wig, lane, 1 + grp, part, parity, &s_frame,
+                    GLD ? I.rhop : s_rp, s_acc, &s_sums, tma);
         __syncthreads();
         if (MODE != kLoglik) {
             for (int rr = warp; rr < tl.RH; rr += kWarps) {
@@ -760,8 +776,9 @@ k_outliers(Geo g, EventsView evs, int first, int count, const float* __restrict_
     const unsigned tma = tm_thread_addr<LMAX>(s_tmem, warp);
     if (grp < ngroups) {
         for (int k = blockIdx.x * ngroups + grp; k < count; k += gridDim.x * ngroups)
-            process_event<LMAX, MODE, NSEG, false>(g, evs, first + k, G, wig, lane, 1 + grp, part,
-                                                   parity, &s_frame, rhop, A, &s_sums, tma);
+            process_event<LMAX, MODE, NSEG, false, false, true>(g, evs, first + k, G, wig, lane,
+                                                                1 + grp, part, parity, &s_frame,
+                                                                rhop, A, &s_sums, tma);
     }
     tm_sync_threads();
     flush_block_sums(&s_sums, accum, MODE);
@@ -803,9 +820,9 @@ k_outliers_batch(const Inst* __restrict__ table, const int4* __restrict__ items,
         int parity = 0;
         if (grp < ngroups)
             for (int k = grp; k < item.z; k += ngroups)
-                process_event<LMAX, MODE, NSEG, false>(s_inst.g, s_inst.evs, item.y + k, G, wig,
-                                                       lane, 1 + grp, part, parity, &s_frame,
-                                                       s_inst.rhop, s_inst.A, &s_sums, tma);
+                process_event<LMAX, MODE, NSEG, false, false, true>(
+                    s_inst.g, s_inst.evs, item.y + k, G, wig, lane, 1 + grp, part, parity,
+                    &s_frame, s_inst.rhop, s_inst.A, &s_sums, tma);
         __syncthreads();
         flush_block_sums(&s_sums, s_inst.accum, MODE);
     }

@@ -25,9 +25,14 @@ cudaError_t run_pass(const PassArgs& a, cudaStream_t st)
         p.accum = a.accum;
         p.G = a.G;
         p.pad = 0;
-        k_tiles<LMAX, MODE, NSEG, false, GLD>
-            <<<a.grid, pass_threads(LMAX, MODE, NSEG, false), a.smem, st>>>(
-            p, nullptr, a.items, a.n_items, &a.accum->queue);
+        if (a.g.kz != 0.0f)
+            k_tiles<LMAX, MODE, NSEG, false, GLD, true>
+                <<<a.grid, pass_threads(LMAX, MODE, NSEG, false), a.smem, st>>>(
+                p, nullptr, a.items, a.n_items, &a.accum->queue);
+        else
+            k_tiles<LMAX, MODE, NSEG, false, GLD, false>
+                <<<a.grid, pass_threads(LMAX, MODE, NSEG, false), a.smem, st>>>(
+                p, nullptr, a.items, a.n_items, &a.accum->queue);
     }
     if (a.outlier_count > 0) {
         const int per_block = group_count(pass_threads(LMAX, MODE, NSEG, false) / 32, a.G);
@@ -39,14 +44,22 @@ cudaError_t run_pass(const PassArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <int LMAX, int MODE, int NSEG, bool GLD, bool KZ>
+cudaError_t set_smem_one(size_t smem)
+{
+    return cudaFuncSetAttribute(k_tiles<LMAX, MODE, NSEG, false, GLD, KZ>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 template <int LMAX, int MODE, int NSEG>
 cudaError_t set_smem(size_t smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_tiles<LMAX, MODE, NSEG, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess && NSEG == 2)
-        e = cudaFuncSetAttribute(k_tiles<LMAX, MODE, NSEG, false, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_smem_one<LMAX, MODE, NSEG, false, false>(smem);
+    if (e == cudaSuccess) e = set_smem_one<LMAX, MODE, NSEG, false, true>(smem);
+    if constexpr (NSEG == 2) {
+        if (e == cudaSuccess) e = set_smem_one<LMAX, MODE, NSEG, true, false>(smem);
+        if (e == cudaSuccess) e = set_smem_one<LMAX, MODE, NSEG, true, true>(smem);
+    }
     return e;
 }
 

@@ -66,11 +66,12 @@ __global__ void k_prepare_chunk(Geo g, long long n, const float* __restrict__ zu
         int2 rw = make_int2(0, 0);
         if (direct_reconstruction(g, zu[j], zd[j], dl[j], e64)) {
             ev = make_float4((float)e64.x, (float)e64.y, (float)e64.z, (float)e64.w);
+            const EvSig es = ev_sig(g, ev);
             int iy_lo, nrows, iz_lo, ncols;
-            event_bbox(g, ev, iy_lo, nrows, iz_lo, ncols);
+            event_bbox(g, es, ev, iy_lo, nrows, iz_lo, ncols);
             int first = -1, last = -1;
             for (int r = 0; r < nrows; ++r) {
-                const Chord c = row_chord(g, ev, &e64, iy_lo + r);
+                const Chord c = row_chord(g, es, ev, &e64, iy_lo + r);
                 if (c.count > 0) {
                     if (first < 0) first = iy_lo + r;
                     last = iy_lo + r;
@@ -106,7 +107,8 @@ int geometry(const tsp_params& p, Geo& g, int& lmax, int& nseg, int& G, char* er
     const double dz = p.dz > 0 ? p.dz : p.L / p.nz;
     const double cut = p.cut > 0 ? p.cut : 3.0;
     g = make_geo(p);
-    const int need = (int)std::floor(2.0 * cut * p.sigma_z / std::sqrt(2.0) / dz) + 2;
+    const int need =
+        (int)std::floor(2.0 * cut * p.sigma_z * (1.0 + p.kappa_z) / std::sqrt(2.0) / dz) + 2;
     lmax = 0;
     for (int k = 0; k < kLmaxCount && !lmax; ++k)
         if (kLmaxList[k] >= need) {

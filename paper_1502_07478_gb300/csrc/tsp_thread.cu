@@ -22,20 +22,21 @@ k_thread_events(Geo g, EventsView evs, int n, const float* __restrict__ rhop,
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         const float4 ev = evs.geo[j];
         const int2 rws = evs.rows[j];
+        const EvSig es = ev_sig(g, ev);
         float D = 0.0f, invD = 0.0f;
         for (int pass = 0; pass < 2; ++pass) {
             for (int r = 0; r < rws.y; ++r) {
                 const int iy = rws.x + r;
-                const Chord c = row_chord(g, ev, evs.geo64 + j, iy);
+                const Chord c = row_chord(g, es, ev, evs.geo64 + j, iy);
                 if (c.count == 0) continue;
                 float Qc, gam2, alpha, beta;
-                row_q(g, ev, c, Qc, gam2);
-                row_acb(g, ev, c, alpha, beta);
+                row_q(g, es, ev, c, Qc, gam2);
+                row_acb(g, es, ev, c, alpha, beta);
                 const float u0 = fmaf((float)c.lo, g.dz, g.z0) - c.zc;
                 const float Q0 = fmaf(gam2, u0, Qc), dQ = gam2 * g.dz;
                 const float A0 = g.kA * fmaf(alpha, u0, beta), dA = g.kA * alpha * g.dz;
-                const float su0 = g.ksu * u0, dsu = g.ksu * g.dz;
-                const float C0 = g.log2K - g.half_log2e * c.B0;
+                const float su0 = es.ksu * u0, dsu = es.ksu * g.dz;
+                const float C0 = es.log2K - g.half_log2e * c.B0;
                 const size_t base = (size_t)iy * g.nz + c.lo;
                 for (int k = 0; k < c.count; ++k) {
                     const float fd = (float)k;

@@ -47,7 +47,7 @@ class Recon:
 
     def __init__(self, R: float, L_: float, ny: int, nz: int, sigma_z: float, sigma_dl: float,
                  cut: float = 3.0, dy: float = 0.0, dz: float = 0.0, device: Optional[int] = None,
-                 gamma: float = 0.0):
+                 gamma: float = 0.0, kappa_z: float = 0.0):
         self._lib = L.lib()
         if torch is not None and torch.cuda.is_available():
             if device is not None:
@@ -55,7 +55,8 @@ class Recon:
             torch.cuda.init()
         self.ny, self.nz = int(ny), int(nz)
         self.params = L.Params(float(R), float(L_), self.ny, self.nz, float(dy), float(dz),
-                               float(sigma_z), float(sigma_dl), float(cut), 0, 0, float(gamma))
+                               float(sigma_z), float(sigma_dl), float(cut), 0, 0, float(gamma),
+                               float(kappa_z))
         h = C.c_void_p()
         rc = self._lib.tsp_create(C.byref(self.params), C.byref(h))
         L.check(None, rc)
@@ -246,9 +247,9 @@ def _sched_dict(s) -> dict:
     return {"ty_cap": s.ty_cap, "items_per_sm": s.items_per_sm, "order": s.order}
 
 
-def _params(R, L_, ny, nz, sigma_z, sigma_dl, cut=3.0, dy=0.0, dz=0.0, gamma=0.0):
+def _params(R, L_, ny, nz, sigma_z, sigma_dl, cut=3.0, dy=0.0, dz=0.0, gamma=0.0, kappa_z=0.0):
     return L.Params(float(R), float(L_), int(ny), int(nz), float(dy), float(dz), float(sigma_z),
-                    float(sigma_dl), float(cut), 0, 0, float(gamma))
+                    float(sigma_dl), float(cut), 0, 0, float(gamma), float(kappa_z))
 
 
 class Batch:
@@ -271,7 +272,7 @@ class Batch:
                          sigma_dl=p.sigma_dl, cut=p.cut)
             plist.append(_params(p["R"], p["L"], p["ny"], p["nz"], p["sigma_z"], p["sigma_dl"],
                                  p.get("cut", 3.0), p.get("dy", 0.0), p.get("dz", 0.0),
-                                 p.get("gamma", 0.0)))
+                                 p.get("gamma", 0.0), p.get("kappa_z", 0.0)))
         if not plist:
             raise ValueError("a batch needs at least one reconstruction")
         self.params = (L.Params * len(plist))(*plist)

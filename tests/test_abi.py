@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_struct_layouts_match_header():
-    assert C.sizeof(L.Params) == 8 * 2 + 4 * 2 + 8 * 5 + 4 * 2 + 8
+    assert C.sizeof(L.Params) == 8 * 2 + 4 * 2 + 8 * 5 + 4 * 2 + 8 + 8
     assert C.sizeof(L.Stats) == 8 * 10
     assert C.sizeof(L.Schedule) == 4 * 4
 
@@ -52,7 +52,7 @@ def test_version(lib):
 
 def _params(**kw):
     base = dict(R=350.0, L=500.0, ny=140, nz=100, dy=0.0, dz=0.0, sigma_z=10.0,
-                sigma_dl=42.0, cut=3.0, flags=0, reserved=0, gamma=0.0)
+                sigma_dl=42.0, cut=3.0, flags=0, reserved=0, gamma=0.0, kappa_z=0.0)
     base.update(kw)
     return L.Params(**base)
 
@@ -60,7 +60,10 @@ def _params(**kw):
 @pytest.mark.parametrize("bad", [dict(R=0.0), dict(L=-1.0), dict(ny=0), dict(nz=-3),
                                  dict(sigma_z=0.0), dict(sigma_dl=float("nan")),
                                  dict(cut=-1.0), dict(flags=1), dict(dy=-1.0),
-                                 dict(gamma=float("nan")), dict(gamma=2e-3)])
+                                 dict(gamma=float("nan")), dict(gamma=2e-3),
+                                 dict(kappa_z=-0.1), dict(kappa_z=1.5),
+                                 dict(kappa_z=float("inf")),
+                                 dict(gamma=1.4e-3, kappa_z=0.5)])
 def test_create_rejects_bad_params(lib, bad):
     h = C.c_void_p(123)
     p = _params(**bad)

@@ -84,6 +84,25 @@ def test_batch_matches_plain_contexts(mixed):
     b.close()
 
 
+def test_batch_with_z_dependent_sigma_matches_oracle(mixed):
+    """Members with different z profiles of sigma_z (kappa_z 0, 0.3, 0.15)
+    share the batched launches and each follows its oracle."""
+    from paper_1502_07478_gb300 import Batch
+    ws, evs = mixed
+    kz = [0.0, 0.3, 0.15]
+    params = [dict(R=w.R, L=w.L, ny=w.ny, nz=w.nz, sigma_z=w.sigma_z, sigma_dl=w.sigma_dl,
+                   cut=w.cut, kappa_z=k) for w, k in zip(ws, kz)]
+    b = Batch(params)
+    for i in range(len(kz)):
+        b.upload_events(i, *evs[i])
+    b.iterate(4)
+    imgs = _images(b, ws[:len(kz)])
+    b.close()
+    for i, k in enumerate(kz):
+        ref, _ = oracle.mlem(Setup.from_workload(ws[i], kappa_z=k), evs[i], 4)
+        assert rel_err(imgs[i], ref) <= TOL, (i, k)
+
+
 def test_iterations_split_and_launch_count(mixed):
     """2 + 3 iterations equal 5; each iteration is a fixed number of launches
     whatever the number of reconstructions: reset, one persistent tile pass per

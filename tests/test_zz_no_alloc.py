@@ -58,6 +58,34 @@ def test_noalloc_update_matches_iterate():
         rho, out = out, rho          # the next call starts from this call's output
 
 
+def test_noalloc_update_with_kappa_matches_iterate():
+    """The same with sigma_z growing towards the strip ends (kappa_z = 0.3)."""
+    import torch
+    from paper_1502_07478_gb300 import Recon
+    from paper_1502_07478_gb300 import _lib as L
+    from synth import make_workload
+
+    w = make_workload("small_5mm")
+    ev = w.events()
+    r = Recon.from_workload(w, kappa_z=0.3)
+    r.upload_events(*ev)
+    s = r.compute_sensitivity()
+    dev_ev = [torch.from_numpy(e).cuda() for e in ev]
+    rho = torch.ones(w.ny, w.nz, dtype=torch.float32, device="cuda")
+    out = torch.empty_like(rho)
+    err = C.create_string_buffer(256)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = L.lib().tsp_mlem_update_noalloc(C.byref(r.params), *(_ptr(e) for e in dev_ev),
+                                         len(ev[0]), _ptr(s), _ptr(rho), _ptr(out), stream,
+                                         err, len(err))
+    assert rc == 0, err.value
+    r.iterate(1)
+    ref = r.read_image()
+    torch.cuda.synchronize()
+    assert _rel_err(out, ref) <= TOL
+    r.close()
+
+
 def test_noalloc_rejects_images_beyond_the_scratch():
     import torch
     from paper_1502_07478_gb300 import _lib as L
