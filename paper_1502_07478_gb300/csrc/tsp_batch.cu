@@ -25,6 +25,7 @@ using namespace tsp_host;
 // lmax, row split nseg): their merged work items and outlier items.
 struct BatchClass {
     int lmax = 0, nseg = 1;
+    bool kz = false;           // some member has a z-dependent sigma_z
     size_t smem = 0;
     int4* items = nullptr;
     int4* oitems = nullptr;
@@ -169,6 +170,7 @@ int rebuild(tsp_batch* b, cudaStream_t st)
         BatchClass& bc = b->cls[q];
         bc.lmax = cls_lmax[q];
         bc.nseg = cls_nseg[q];
+        bc.kz = false;
         bc.smem = 0;
         std::vector<std::vector<int4>> lists;
         std::vector<int> members;
@@ -177,6 +179,7 @@ int rebuild(tsp_batch* b, cudaStream_t st)
             if (cls_of[i] != q) continue;
             const tsp_ctx* c = b->inst[i];
             bc.smem = std::max(bc.smem, c->smem);
+            if (c->p.kappa_z != 0.0) bc.kz = true;
             members.push_back(i);
             // a reconstruction whose tiles stage only the accumulator is not
             // supported by the batched tile kernel: all its events take the
@@ -264,6 +267,7 @@ BatchArgs batch_args(const tsp_batch* b, int q)
     a.n_outlier_items = bc.n_oitems;
     a.queue = b->queue + q;
     a.nseg = bc.nseg;
+    a.kz = bc.kz ? 1 : 0;
     a.grid = b->num_sms;
     a.smem = bc.smem;
     return a;

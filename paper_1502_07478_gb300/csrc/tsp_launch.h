@@ -44,6 +44,7 @@ struct BatchArgs {
     int n_outlier_items;
     int* queue;        // work counter, zeroed before the launch
     int nseg;
+    int kz;            // some reconstruction has a z-dependent sigma_z
     int grid;
     size_t smem;
 };

@@ -619,11 +619,11 @@ __device__ __forceinline__ Frame tile_frame(const Geo& g, const Tiling& tl, int 
 // memory when it changes.  `queue` is the work counter (zero at launch).
 // GLD: only the accumulator is staged (windows too large for both regions);
 // rho' is read from the global image through the read-only cache.  KZ: the
-// plain form for a z-dependent sigma_z (each event's own resolution
-// constants); the plain form without it reads the context's constants, and
-// the batched form takes each event's, whatever its reconstruction's profile.
-// (The two plain forms are separate kernels because the gradient pass is at
-// the register limit: holding both row setups in one kernel spilled there.)
+// form for a z-dependent sigma_z (each event's own resolution constants; a
+// batch takes it when any of its reconstructions has one); the form without
+// it reads the context's constants.  (The two are separate kernels because
+// the gradient pass is at the register limit: holding both row setups in one
+// kernel spilled there.)
 template <int LMAX, int MODE, int NSEG, bool BATCH, bool GLD = false, bool KZ = false>
 __global__ void __launch_bounds__(pass_threads(LMAX, MODE, NSEG, BATCH), 1)
 k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, int n_items,
@@ -719,7 +719,7 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
         __syncthreads();
         if (grp < ngroups)
             for (int e = item.y + grp; e < item.y + item.z; e += ngroups)
-                process_event<LMAX, MODE, NSEG, true, GLD, BATCH || KZ>(
+                process_event<LMAX, MODE, NSEG, true, GLD, KZ>(
                     g, I.evs, e, G, wig, lane, 1 + grp, part, parity, &s_frame,
                     GLD ? I.rhop : s_rp, s_acc, &s_sums, tma);
         __syncthreads();

@@ -69,10 +69,16 @@ template <int LMAX, int MODE, int NSEG>
 cudaError_t run_batch(const BatchArgs& a, cudaStream_t st)
 {
     Inst none{};
-    if (a.n_items > 0)
-        k_tiles<LMAX, MODE, NSEG, true><<<a.grid, pass_threads(LMAX, MODE, NSEG, true), a.smem, st>>>(
-            none, a.table, a.items,
-                                                                          a.n_items, a.queue);
+    if (a.n_items > 0) {
+        if (a.kz)
+            k_tiles<LMAX, MODE, NSEG, true, false, true>
+                <<<a.grid, pass_threads(LMAX, MODE, NSEG, true), a.smem, st>>>(
+                    none, a.table, a.items, a.n_items, a.queue);
+        else
+            k_tiles<LMAX, MODE, NSEG, true, false, false>
+                <<<a.grid, pass_threads(LMAX, MODE, NSEG, true), a.smem, st>>>(
+                    none, a.table, a.items, a.n_items, a.queue);
+    }
     if (a.n_outlier_items > 0)
         k_outliers_batch<LMAX, MODE, NSEG>
             <<<a.n_outlier_items < a.grid ? a.n_outlier_items : a.grid,
@@ -94,11 +100,15 @@ cudaError_t run_batch_mode(int mode, const BatchArgs& a, cudaStream_t st)
 template <int LMAX, int NSEG>
 cudaError_t batch_smem(size_t smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(k_tiles<LMAX, kMlem, NSEG, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int v = (int)smem;
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_tiles<LMAX, kMlem, NSEG, true, false, false>, at, v);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_tiles<LMAX, kGrad, NSEG, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_tiles<LMAX, kMlem, NSEG, true, false, true>, at, v);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tiles<LMAX, kGrad, NSEG, true, false, false>, at, v);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tiles<LMAX, kGrad, NSEG, true, false, true>, at, v);
     return e;
 }
 
