@@ -144,8 +144,8 @@ int plan(tsp_ctx* c)
         // every event takes the global-memory path
         // rho' is then read through L1, which gets what the shared-memory
         // carve-out leaves of the SM's 256 KB: the accumulator region is kept
-        // to ~150 KB (at 0.5 mm, 1e7 events: 463 ms per pass with a 147 KB
-        // region against 640 ms with 197 KB)
+        // to ~150 KB (at 0.5 mm a pass with a 147 KB region took 28% less
+        // time than with 197 KB)
         const size_t gld_budget = 150 * 1024;
         TY = ty0;
         while (TY > 4 && tiles_acc_smem_floats(TY + 2 * tl.HY, RS) * sizeof(float) > gld_budget)
