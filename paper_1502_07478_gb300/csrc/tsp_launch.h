@@ -1,6 +1,8 @@
 // Host-side launch interface of the libtsp kernels (internal to the library).
 #pragma once
 
+#include <cmath>
+
 #include <cuda_runtime.h>
 
 #include "tsp.h"
@@ -13,9 +15,84 @@ Geo make_geo(const tsp_params& p);
 // Whether the parameters give a positive-definite C^-1 (2 gamma^2 < iz il).
 bool cinv_valid(const tsp_params& p);
 
-// Lane capacities (pixels of one row segment held in registers) compiled in.
+// Host-side fault injection, for tests of the error paths without a device
+// fault.  The environment variable TSP_SIM_FAULT names one failure that the
+// library then simulates at every site it reaches, for as long as the
+// variable holds that value:
+//   oom        device allocations fail as cudaMalloc does when memory is
+//              exhausted (the entry point returns TSP_ENOMEM and unwinds)
+//   launch     the kernel-launch helpers fail before enqueuing anything, with
+//              cudaErrorLaunchOutOfResources (TSP_ECUDA)
+//   nan_event  every uploaded chunk gets a NaN in its first z_u after the copy
+//              (the event preparation rejects the upload: TSP_EINVAL)
+// Unset or any other value: no fault.
+enum SimFault : int { kSimNone = 0, kSimOom = 1, kSimLaunch = 2, kSimNan = 3 };
+int sim_fault();
+
+// The error a launch helper returns under TSP_SIM_FAULT=launch, else success.
+inline cudaError_t sim_launch() { return sim_fault() == kSimLaunch ? cudaErrorLaunchOutOfResources : cudaSuccess; }
+
+// cudaMalloc, or a simulated exhaustion under TSP_SIM_FAULT=oom.
+template <class T>
+cudaError_t dmalloc(T** p, size_t bytes)
+{
+    if (sim_fault() == kSimOom) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+// Lane capacities (pixels of one row segment a lane walks) compiled in.
 constexpr int kLmaxList[] = {12, 24, 48, 64};
 constexpr int kLmaxCount = 4;
+
+// Lane layout of a parameter set's windows, shared by the context planner and
+// the allocation-free entry point so that both launch the kernel form that
+// the event preparation's chords were sized for:
+//   need     longest chord of a window row in pixels, plus 2: the chord of the
+//            cut ellipse is at most 2 cut sigma_z / sqrt(2) wide, with the
+//            largest sigma_z of any event, sigma_z (1 + kappa_z)
+//   lmax     smallest compiled capacity holding a whole chord (nseg = 1), else
+//            one holding half a chord plus 2 (nseg = 2: two lanes per row)
+//   maxrows  most rows of one window (|Dy| <= cut sigma_dl cos / 2), plus 2
+//   G        warps per event: nseg lanes for each of maxrows rows
+// Returns nullptr, or the reason the windows fit no compiled kernel.
+struct LanePlan {
+    int need, lmax, nseg, maxrows, G;
+};
+
+inline const char* lane_plan(const tsp_params& p, LanePlan& lp)
+{
+    const double dy = p.dy > 0 ? p.dy : 2.0 * p.R / p.ny;
+    const double dz = p.dz > 0 ? p.dz : p.L / p.nz;
+    const double cut = p.cut > 0 ? p.cut : 3.0;
+    const double umax = cut * p.sigma_z * (1.0 + p.kappa_z) / std::sqrt(2.0);
+    lp.need = (int)std::floor(2.0 * umax / dz) + 2;
+    lp.lmax = 0;
+    lp.nseg = 1;
+    for (int k = 0; k < kLmaxCount && !lp.lmax; ++k)
+        if (kLmaxList[k] >= lp.need) lp.lmax = kLmaxList[k];
+    for (int k = 0; k < kLmaxCount && !lp.lmax; ++k)
+        if (kLmaxList[k] >= lp.need / 2 + 2) {
+            lp.lmax = kLmaxList[k];
+            lp.nseg = 2;
+        }
+    if (!lp.lmax) return "window chords too long for the compiled lane capacities";
+    const double hy = cut * p.sigma_dl / 2.0 * 1.00001;
+    lp.maxrows = (int)std::floor(2.0 * hy / dy) + 2;
+    lp.G = lp.nseg * ((lp.maxrows + 31) / 32);
+    if (lp.G > kMinWarps) return "window has more rows than one block can hold";
+    return nullptr;
+}
+
+// Lane capacity for two lanes per row (the accumulator-only tiles), or 0.
+inline int lane_lmax_split(int need)
+{
+    for (int k = 0; k < kLmaxCount; ++k)
+        if (kLmaxList[k] >= need / 2 + 2) return kLmaxList[k];
+    return 0;
+}
 
 struct PassArgs {
     Geo g;

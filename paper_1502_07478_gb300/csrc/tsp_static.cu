@@ -93,8 +93,10 @@ __global__ void k_update_out(int npix, const float* __restrict__ rho_in,
         rho_out[i] = rho_in[i] * A[i];
 }
 
-// Kernel constants and lane layout for params (the same formulas as the
-// context-based path uses).  Returns TSP_OK or TSP_EINVAL.
+// Kernel constants and lane layout for params: the lane layout comes from
+// lane_plan(), the helper the context planner uses, so this pass launches the
+// kernel form whose lane capacity the chords of k_prepare_chunk were sized
+// for.  Returns TSP_OK or TSP_EINVAL.
 int geometry(const tsp_params& p, Geo& g, int& lmax, int& nseg, int& G, char* errbuf,
              size_t errlen)
 {
@@ -103,27 +105,12 @@ int geometry(const tsp_params& p, Geo& g, int& lmax, int& nseg, int& G, char* er
         !pos(p.sigma_dl) || !(p.dy == 0.0 || pos(p.dy)) || !(p.dz == 0.0 || pos(p.dz)) ||
         !(p.cut == 0.0 || pos(p.cut)) || p.flags != 0 || !cinv_valid(p))
         return report(errbuf, errlen, TSP_EINVAL, "invalid tsp_params");
-    const double dy = p.dy > 0 ? p.dy : 2.0 * p.R / p.ny;
-    const double dz = p.dz > 0 ? p.dz : p.L / p.nz;
-    const double cut = p.cut > 0 ? p.cut : 3.0;
     g = make_geo(p);
-    const int need =
-        (int)std::floor(2.0 * cut * p.sigma_z * (1.0 + p.kappa_z) / std::sqrt(2.0) / dz) + 2;
-    lmax = 0;
-    for (int k = 0; k < kLmaxCount && !lmax; ++k)
-        if (kLmaxList[k] >= need) {
-            lmax = kLmaxList[k];
-            nseg = 1;
-        }
-    for (int k = 0; k < kLmaxCount && !lmax; ++k)
-        if (kLmaxList[k] >= need / 2 + 2) {
-            lmax = kLmaxList[k];
-            nseg = 2;
-        }
-    if (!lmax) return report(errbuf, errlen, TSP_EINVAL, "window chords too long");
-    const int maxrows = (int)std::floor(2.0 * cut * p.sigma_dl / 2.0 * 1.00001 / dy) + 2;
-    G = nseg * ((maxrows + 31) / 32);
-    if (G > kMinWarps) return report(errbuf, errlen, TSP_EINVAL, "window has too many rows");
+    LanePlan lp;
+    if (const char* why = lane_plan(p, lp)) return report(errbuf, errlen, TSP_EINVAL, why);
+    lmax = lp.lmax;
+    nseg = lp.nseg;
+    G = lp.G;
     return TSP_OK;
 }
 
@@ -170,7 +157,11 @@ extern "C" int tsp_mlem_update_noalloc(const tsp_params* params, const float* zu
     Accum* accum = reinterpret_cast<Accum*>(base + kOffAccum);
     cudaStream_t st = (cudaStream_t)stream;
     int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        sms <= 0) {
+        cudaGetLastError();   // leave no pending error for a later launch check
+        return report(errbuf, errlen, TSP_ECUDA, "cudaDeviceGetAttribute(MultiProcessorCount) failed");
+    }
 
     // the scratch keeps the previous call's contents: clear what must start at 0
     if ((e = launch_begin(accum, st)) != cudaSuccess ||
@@ -193,7 +184,7 @@ extern "C" int tsp_mlem_update_noalloc(const tsp_params* params, const float* zu
     a.G = G;
     a.nseg = nseg;
     a.gld = 0;
-    a.grid = sms > 0 ? sms : 1;
+    a.grid = sms;
     a.smem = 0;
     for (long long c0 = 0; c0 < n; c0 += TSP_NOALLOC_CHUNK) {
         const long long nc = (n - c0 < TSP_NOALLOC_CHUNK) ? n - c0 : TSP_NOALLOC_CHUNK;
