@@ -494,7 +494,17 @@ int orc_update_at_pixels(const orc_params* p, const double* zu, const double* zd
 {
     int nt = nthreads_of(p);
     double* part = (double*)calloc((size_t)nt * npx, sizeof(double));
-    if (!part) return -1;
+    /* slot[i] = the position in pix of image pixel i (its first occurrence),
+     * or -1: finds a window pixel's place in the list without a search */
+    int64_t npix = (int64_t)p->ny * p->nz;
+    int32_t* slot = (int32_t*)malloc((size_t)npix * sizeof(int32_t));
+    if (!part || !slot) {
+        free(part);
+        free(slot);
+        return -1;
+    }
+    for (int64_t i = 0; i < npix; ++i) slot[i] = -1;
+    for (int32_t q = npx - 1; q >= 0; --q) slot[pix[q]] = q;
     double cut2 = p->cut * p->cut;
 #ifdef _OPENMP
 #pragma omp parallel num_threads(nt)
@@ -523,20 +533,22 @@ int orc_update_at_pixels(const orc_params* p, const double* zu, const double* zd
             double D = 0.0;
             for (int64_t k = 0; k < m; ++k) D += c.P[k] * s[c.idx[k]] * rho[c.idx[k]];
             if (!(D > 0.0)) continue;
-            for (int64_t k = 0; k < m; ++k)
-                for (int q = 0; q < npx; ++q)
-                    if (c.idx[k] == pix[q])
-                        part[(int64_t)tid * npx + q] += rho[pix[q]] * c.P[k] / D;
+            for (int64_t k = 0; k < m; ++k) {
+                int32_t q = slot[c.idx[k]];
+                if (q >= 0) part[(int64_t)tid * npx + q] += rho[pix[q]] * c.P[k] / D;
+            }
         }
         free(c.idx);
         free(c.P);
     }
     for (int q = 0; q < npx; ++q) {
         double v = 0.0;
-        for (int k = 0; k < nt; ++k) v += part[(int64_t)k * npx + q];
+        int32_t q0 = slot[pix[q]];     /* a repeated pixel takes its first entry's sum */
+        for (int k = 0; k < nt; ++k) v += part[(int64_t)k * npx + q0];
         out[q] = v;
     }
     free(part);
+    free(slot);
     return 0;
 }
 

@@ -79,7 +79,9 @@ def test_update_at_pixels_matches_full_update(small):
     st, ev, s = small
     rho0, _ = oracle.mlem(st, ev, 2, s=s)
     rho1, _ = oracle.mlem(st, ev, 1, rho0=rho0, s=s)
-    pix = np.array([0, 777, 7050, 7051, 13999, 5000])
+    # scattered pixels, a repeated one, and a compact 4 x 4 patch
+    patch = [(60 + a) * 100 + 40 + b for a in range(4) for b in range(4)]
+    pix = np.array([0, 777, 7050, 7051, 13999, 5000, 777] + patch)
     got = oracle.update_at_pixels(st, ev, rho0, pix, s=s)
     np.testing.assert_allclose(got, rho1.ravel()[pix], rtol=1e-12, atol=1e-300)
 
