@@ -15,13 +15,21 @@ another, images compared), the adjoint pass on the 2 mm workload, the same
 metric end to end through the C ABI with host buffers
 (e2e: pinned-host event upload, per-event preparation and binning, the
 iterations and the image readout, every step), the dominant kernel's achieved
-pixel-evaluation rate against the SFU (MUFU) roofline, and the FP64 CPU oracle
-timed on the host's cores on a bounded sample of the same workload.
+pixel-evaluation rate against its roofline (max of the SFU and FMA-pipe time
+per evaluation), the FP64 CPU oracle timed on the host's cores on a bounded
+sample of the same workload, and a stress record: the 1e8-event 0.5 mm
+workload streamed in pinned 1e7-event chunks (one timed step of 10
+iterations, with its own roofline) and the adjoint pass of 16 reconstructions
+batched against 16 plain passes.  The stress inputs are generated by a spawned
+process pool while the main leg runs.
 
 ``--impl reference`` times the FP64 CPU oracle instead (the reference arm).
-Multi-GPU (torchrun, one rank per GPU): each rank reconstructs its own
-independent event set (a different seed); no collective touches the data
-path; value is the sum over ranks divided by the slowest rank's time.
+Multi-GPU (torchrun, one rank per GPU): one reconstruction whose events are
+sharded over the ranks -- rank r holds its own seeded share of the event count
+(weak scaling: the list grows with the ranks) -- and every iteration is a
+back-projection on each rank, an NCCL all-reduce (sum) of the back-projection
+and the same image update on every rank; value is the events of all ranks x
+iterations / the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -40,12 +48,52 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLEM event-iterations/s (1e7 events, 1 mm grid), batched vs plain, rel err <=1e-4"
 UNIT = "event-iterations/s"
-MUFU_PER_PIXEL = 2          # one rsqrt and one ex2 per in-window pixel (pass 1)
-MUFU_PER_SM_CLK = 16        # SFU results per SM per clock (sm_100-class)
+# Roofline of the MLEM pass (one unit = one in-window pixel evaluation of the
+# kernel P; the count W per launch is exact, from the event preparation).  The
+# algorithmic work per unit: 2 SFU operations (one rsqrt, one ex2) and 17
+# FMA-pipe operations (the kernel's quadratic forms, the exponent, P, the
+# denominator sum and the scatter's product, row constants amortised).
+# Per-SM rates per clock: 128 FP32 FMA lanes; the SFU rates measured by
+# microbenchmark on this GB300 (rsqrt.approx 15.9, ex2.approx 31.7).  The pass
+# cannot beat max(SFU time, FMA time) per unit.
+SFU_RSQRT_PER_SM_CLK = 15.9
+SFU_EX2_PER_SM_CLK = 31.7
+FMA_PER_SM_CLK = 128
+FMA_OPS_PER_PIXEL = 17
 # DRAM bytes per event of one MLEM tile pass (dram__bytes_read.sum +
-# dram__bytes_write.sum of one launch over 1e6 events of the 1 mm workload,
-# profiles/k_tiles_paper_1mm_1e6.md); the traffic grows with the events.
+# dram__bytes_write.sum of one ncu-captured launch over 1e6 events of the
+# 1 mm workload); the traffic grows with the events.
 TILE_PASS_DRAM_B_PER_EVENT = 47.8
+
+
+def roofline_basis(device: int):
+    """Peak pixel-evaluation rate of the MLEM pass on this device (per second)
+    and the formula behind it."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    f = float(_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+    t_sfu = 1.0 / SFU_RSQRT_PER_SM_CLK + 1.0 / SFU_EX2_PER_SM_CLK     # clocks per unit per SM
+    t_fma = FMA_OPS_PER_PIXEL / FMA_PER_SM_CLK
+    return {"peak": sms * f / max(t_sfu, t_fma), "sfu_only": sms * f / t_sfu,
+            "basis": f"{sms} SMs x {f/1e6:.0f} MHz / max(1/{SFU_RSQRT_PER_SM_CLK} + "
+                     f"1/{SFU_EX2_PER_SM_CLK} SFU clk, {FMA_OPS_PER_PIXEL}/{FMA_PER_SM_CLK} "
+                     f"FMA clk) per pixel evaluation"}
+
+
+def roofline_dict(W, t_pass, basis, kernel, traffic=None):
+    """The bench line's roofline object for a pass of W pixel evaluations
+    taking t_pass seconds (None when not timed)."""
+    achieved = W / t_pass if t_pass else None
+    return {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
+            "peak": basis["peak"] / 1e9, "unit": "Gpixel-evals/s",
+            "frac": achieved / basis["peak"] if achieved else None,
+            "frac_of_sfu_bound": achieved / basis["sfu_only"] if achieved else None,
+            "traffic": traffic,
+            "traffic_basis": ("ncu DRAM bytes of one 1e6-event launch, scaled by events"
+                              if traffic is not None else None),
+            "kernel": kernel, "pixel_evals_per_launch": W,
+            "launch_ms": t_pass * 1e3 if t_pass else None,
+            "peak_basis": basis["basis"]}
 
 
 def _peaks():
@@ -314,26 +362,50 @@ def bench_adjoint(reps: int = 5):
             "includes": "rho' refresh, gradient pass, g = s(A - 1), readout of L and g_sigma"}
 
 
-def bench_stress(args, workload, chunk: int = 10_000_000):
-    """The stress workload: 0.5 mm pixels (1400 x 1000), 1e8 events streamed to
-    the device in 1e7-event pinned chunks (tsp_begin/append/end_events), 10
-    iterations; plus the adjoint pass of 16 independent 2 mm reconstructions
-    (1e6 events each) batched in one launch against 16 plain passes.  Warm-up
-    is 3 single iterations; a timed step is the workload's 10 iterations."""
+STRESS_CHUNK = 10_000_000
+ADJ_INSTANCES = 16
+
+
+def _adjoint_instances():
+    from synth import make_workload
+    return [make_workload("adjoint_2mm", seed=4 + 1000 * (i + 1)) for i in range(ADJ_INSTANCES)]
+
+
+def start_stress_inputs(workload, chunk: int = STRESS_CHUNK):
+    """Start generating the stress workload's streamed chunks and the 16 adjoint
+    event sets in a spawned process pool (no GPU use); returns (pool, chunk
+    futures, adjoint futures).  The default run starts this before its main
+    leg so that generation overlaps the GPU timing."""
     import concurrent.futures as cf
     import multiprocessing as mp
     sizes = workload.chunk_sizes(chunk)
-    from synth import make_workload
-    adj = [make_workload("adjoint_2mm", seed=4 + 1000 * (i + 1)) for i in range(16)]
-    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 4),
-                                mp_context=mp.get_context("spawn")) as ex:
-        chunks = list(ex.map(_make_chunk, [(workload.name, workload.n_events, k, chunk)
-                                           for k in range(len(sizes))]))
-        adj_ev = list(ex.map(_make_events, [("adjoint_2mm", w.seed) for w in adj]))
+    ex = cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 4),
+                                mp_context=mp.get_context("spawn"))
+    cf_chunks = [ex.submit(_make_chunk, (workload.name, workload.n_events, k, chunk))
+                 for k in range(len(sizes))]
+    cf_adj = [ex.submit(_make_events, ("adjoint_2mm", w.seed)) for w in _adjoint_instances()]
+    return ex, cf_chunks, cf_adj
+
+
+def stress_record(workload, inputs, steps: int, warmup_iters: int, with_e2e: bool,
+                  chunk: int = STRESS_CHUNK):
+    """The stress workload: 0.5 mm pixels (1400 x 1000), 1e8 events streamed to
+    the device in 1e7-event pinned chunks (tsp_begin/append/end_events), 10
+    iterations per step after ``warmup_iters`` single iterations; plus the
+    adjoint pass of 16 independent 2 mm reconstructions (1e6 events each)
+    batched in one launch against 16 plain passes.  Returns the record (dict)
+    with its own roofline for the accumulator-only tile kernel."""
     import torch
     from paper_1502_07478_gb300 import Batch, Recon
+    ex, cf_chunks, cf_adj = inputs
+    chunks = [f.result() for f in cf_chunks]
+    adj_ev = [f.result() for f in cf_adj]
+    ex.shutdown()
+    adj = _adjoint_instances()
+    sizes = workload.chunk_sizes(chunk)
     torch.cuda.set_device(0)
     pinned = [[torch.from_numpy(x).pin_memory() for x in c] for c in chunks]
+    del chunks
     stream = torch.cuda.current_stream()
     n = workload.n_events
     n_iter = workload.n_iter
@@ -350,12 +422,21 @@ def bench_stress(args, workload, chunk: int = 10_000_000):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     upload()
-    r.iterate(n_iter)
-    r.read_image(out=out.numpy())
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
+    t_upload = time.perf_counter() - t0
+    e2e = None
+    if with_e2e:
+        t0 = time.perf_counter()
+        upload()
+        r.iterate(n_iter)
+        r.read_image(out=out.numpy())
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": n * n_iter / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 4 * workload.ny * workload.nz,
+               "steps": 1, "includes": "streamed upload + binning + iterations + readout"}
     r.set_profiling(True)
-    for _ in range(3):
+    for _ in range(warmup_iters):
         r.iterate(1)
     r.set_image(None)
     torch.cuda.synchronize()
@@ -366,7 +447,7 @@ def bench_stress(args, workload, chunk: int = 10_000_000):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         r.set_image(None)
         r.iterate(n_iter)
     e1.record(stream)
@@ -411,14 +492,10 @@ def bench_stress(args, workload, chunk: int = 10_000_000):
 
     W = st1["n_window"]
     t_pass = float(np.mean(pass_ms[-n_iter:])) / 1e3 if pass_ms else float("nan")
-    props = torch.cuda.get_device_properties(0)
-    peaks = _peaks()
-    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    peak = props.multi_processor_count * f_max * MUFU_PER_SM_CLK / MUFU_PER_PIXEL
-    cpu = None if args.no_cpu_baseline else cpu_baseline(workload, target_s=10.0)
-    line = {
-        "metric": METRIC, "value": n * n_iter * args.steps / (ms / 1e3), "unit": UNIT,
-        "n_gpus": 1, "steps": args.steps, "warmup": 3, "ms_per_step": ms / args.steps,
+    roof = roofline_basis(0)
+    return {
+        "metric": METRIC, "value": n * n_iter * steps / (ms / 1e3), "unit": UNIT,
+        "n_gpus": 1, "steps": steps, "warmup": warmup_iters, "ms_per_step": ms / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded phantom events, streamed form: chunk k from seed (5, k))",
         "config": {"workload": workload.name, "events": n, "iterations_per_step": n_iter,
@@ -426,18 +503,14 @@ def bench_stress(args, workload, chunk: int = 10_000_000):
                    "sigma_z": workload.sigma_z, "sigma_dl": workload.sigma_dl,
                    "cut": workload.cut, "form": "plain, streamed upload",
                    "upload": f"{len(sizes)} pinned chunks of <= {chunk} events",
-                   "warmup": "3 single iterations",
+                   "warmup": f"{warmup_iters} single iterations",
                    "l2": "inputs larger than L2", "parallelism": "1 GPU"},
-        "roofline": {"bound": "alu", "achieved": W / t_pass / 1e9 if pass_ms else None,
-                     "peak": peak / 1e9, "unit": "Gpixel-evals/s",
-                     "frac": (W / t_pass / peak) if pass_ms else None, "traffic": None,
-                     "kernel": "k_tiles (accumulator-only tiles, rho' from global), per launch",
-                     "pixel_evals_per_launch": W, "launch_ms": t_pass * 1e3},
-        "cpu_baseline": cpu,
-        "e2e": {"value": n * n_iter / t_e2e, "unit": UNIT,
-                "h2d_bytes_per_step": 12 * n, "d2h_bytes_per_step": 4 * workload.ny * workload.nz,
-                "steps": 1, "includes": "streamed upload + binning + iterations + readout"},
-        "adjoint_batched_16": {"instances": 16, "events": n_adj, "grid": [350, 250],
+        "roofline": roofline_dict(W, t_pass if pass_ms else None, roof,
+                                  "k_tiles (accumulator-only tiles, rho' from global), per launch",
+                                  traffic=None),
+        "upload_s": t_upload,
+        "e2e": e2e,
+        "adjoint_batched_16": {"instances": ADJ_INSTANCES, "events": n_adj, "grid": [350, 250],
                                "batched_s": t_b, "plain_s": t_p, "speedup": t_p / t_b,
                                "events_per_s_batched": n_adj / t_b,
                                "max_rel_err_g_rho_vs_plain": gerr, "max_rel_err_L_vs_plain": Lerr},
@@ -445,7 +518,15 @@ def bench_stress(args, workload, chunk: int = 10_000_000):
         "checks": {"conservation_rel": cons, "n_used": st1["n_used"],
                    "n_outliers": st1["n_outliers"], "n_empty": st1["n_empty"]},
     }
-    print(json.dumps(line), flush=True)
+
+
+def bench_stress(args, workload):
+    """--workload stress_05mm: the stress record as the bench line, with its
+    end-to-end leg and the CPU baseline.  Warm-up is 3 single iterations."""
+    rec = stress_record(workload, start_stress_inputs(workload), steps=args.steps,
+                        warmup_iters=3, with_e2e=True)
+    rec["cpu_baseline"] = None if args.no_cpu_baseline else cpu_baseline(workload, target_s=10.0)
+    print(json.dumps(rec), flush=True)
     return 0
 
 
@@ -462,6 +543,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-vs-plain comparison")
+    ap.add_argument("--no-stress", action="store_true",
+                    help="skip the stress record (1e8 events at 0.5 mm, batched adjoint)")
     ap.add_argument("--variant", default="tiles", choices=["tiles", "thread"],
                     help="MLEM pass: the tile kernel, or one thread per event (ablation)")
     args = ap.parse_args()
@@ -482,6 +565,11 @@ def main():
             print(json.dumps({"error": "the stress workload runs on one GPU"}))
             return 1
         return bench_stress(args, workload)
+    # the stress record's inputs are generated by a spawned pool while the
+    # main leg runs (no GPU use in the pool)
+    stress_inputs = None
+    if ws == 1 and not args.no_stress and args.workload == "paper_1mm" and not args.n_events:
+        stress_inputs = start_stress_inputs(make_workload("stress_05mm"))
     import torch
     if not torch.cuda.is_available():
         print(json.dumps({"error": "no CUDA device"}))
@@ -492,10 +580,11 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
         pg = dist
-    if rank != 0 or ws > 1:
+        # one reconstruction of ws x n events: rank r holds its seeded share
         workload = _replace(workload, seed=workload.seed + 1000 * rank)
 
     from paper_1502_07478_gb300 import Recon
+    from paper_1502_07478_gb300.shard import sharded_iterate
     ev = workload.events()
     n_iter = workload.n_iter
     n = workload.n_events
@@ -506,10 +595,17 @@ def main():
     r.upload_events(*ev)
     r.set_profiling(True)
     stream = torch.cuda.current_stream()
+    buf = torch.empty((workload.ny, workload.nz), dtype=torch.float32, device="cuda")
+
+    def iterations():
+        if pg is None:
+            r.iterate(n_iter)           # graph replay of n_iter updates
+        else:                           # back-projection, NCCL all-reduce, update
+            sharded_iterate(r, n_iter, pg.all_reduce, buf)
 
     def step():
         r.set_image(None)
-        r.iterate(n_iter)
+        iterations()
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -533,51 +629,51 @@ def main():
     pass_ms = r.pass_times()
     st1 = r.stats()
     launches = st1["launches"] - st0["launches"]
+    used = st1["n_used"]
     if pg:
         t = torch.tensor([ms], device="cuda")
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         ms = float(t.item())
+        u = torch.tensor([used], dtype=torch.int64, device="cuda")
+        pg.all_reduce(u)
+        used = int(u.item())
+        # the back-projection alone, for the roofline (no graph, one launch)
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        r.backproject(out=buf)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        pass_ms = [b0.elapsed_time(b1)]
     sec = ms / 1e3
     value = ws * n * n_iter * args.steps / sec
 
     # parity check at the benchmark's own size and launch configuration:
-    # count conservation sum_l s_l rho_l = N_used after the last iteration
+    # count conservation sum_l s_l rho_l = N_used (all ranks) after the last
+    # iteration
     s_map = r.compute_sensitivity().double()
     rho = r.read_image().double()
-    cons = float((s_map * rho).sum()) / max(1, st1["n_used"]) - 1.0
+    cons = float((s_map * rho).sum()) / max(1, used) - 1.0
 
     # dominant kernel: the MLEM tile kernel; algorithmic work = in-window pixel
     # evaluations per launch (exact count from the event preparation)
     W = st1["n_window"]
-    t_pass = float(np.mean(pass_ms)) / 1e3 if pass_ms else float("nan")
-    props = torch.cuda.get_device_properties(local)
-    sms = props.multi_processor_count
-    peaks = _peaks()
-    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    peak = sms * f_max * MUFU_PER_SM_CLK / MUFU_PER_PIXEL
-    achieved = W / t_pass if pass_ms else None
-    roofline = {"bound": "alu", "achieved": achieved / 1e9 if achieved else None,
-                "peak": peak / 1e9, "unit": "Gpixel-evals/s",
-                "frac": (achieved / peak) if achieved else None,
-                "traffic": (TILE_PASS_DRAM_B_PER_EVENT * n
-                            if workload.name == "paper_1mm" and args.variant == "tiles"
-                            else None),
-                "traffic_basis": "ncu DRAM bytes of one 1e6-event launch, scaled by events",
-                "kernel": ("k_tiles" if args.variant == "tiles" else "k_thread_events") +
-                          " (MLEM pass, per launch)", "pixel_evals_per_launch": W,
-                "launch_ms": t_pass * 1e3,
-                "peak_basis": f"{sms} SMs x {f_max/1e6:.0f} MHz x {MUFU_PER_SM_CLK} SFU ops/clk"
-                              f" / {MUFU_PER_PIXEL} SFU ops per pixel evaluation"}
+    t_pass = float(np.mean(pass_ms)) / 1e3 if pass_ms else None
+    roofline = roofline_dict(
+        W, t_pass, roofline_basis(local),
+        ("k_tiles" if args.variant == "tiles" else "k_thread_events") + " (MLEM pass, per launch)",
+        traffic=(TILE_PASS_DRAM_B_PER_EVENT * n
+                 if workload.name == "paper_1mm" and args.variant == "tiles" else None))
 
     e2e = None
     if not args.no_e2e:
-        out = np.empty((workload.ny, workload.nz), np.float32)
         pinned_out = torch.empty((workload.ny, workload.nz), dtype=torch.float32).pin_memory()
         r.set_profiling(False)
 
         def e2e_step():
             r.upload_events(*pinned)
-            r.iterate(n_iter)
+            iterations()
             r.read_image(out=pinned_out.numpy())
 
         e2e_step()
@@ -597,11 +693,15 @@ def main():
         e2e = {"value": ws * n * n_iter * k_e2e / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(sum(p.numel() * 4 for p in pinned)),
                "d2h_bytes_per_step": int(pinned_out.numel() * 4), "steps": k_e2e}
+    r.close()
 
-    batched = adjoint = None
+    batched = adjoint = stress = None
     if not args.no_batched and ws == 1:
         batched = bench_batched(steps=max(1, min(args.steps, 2)), warmup=1)
         adjoint = bench_adjoint()
+    if stress_inputs is not None:
+        stress = stress_record(make_workload("stress_05mm"), stress_inputs, steps=1,
+                               warmup_iters=1, with_e2e=False)
 
     if rank != 0:
         if pg:
@@ -616,18 +716,21 @@ def main():
         "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded phantom events; the paper's event sets are not published)",
-        "config": {"workload": workload.name, "events": n, "iterations_per_step": n_iter,
+        "config": {"workload": workload.name, "events": n * ws, "events_per_gpu": n,
+                   "iterations_per_step": n_iter,
                    "grid": [workload.ny, workload.nz], "pixel_mm": workload.dz,
                    "sigma_z": workload.sigma_z, "sigma_dl": workload.sigma_dl,
                    "cut": workload.cut, "form": "plain",
                    "kernel_variant": args.variant,
                    "l2": "inputs larger than L2 (prepared events 24 B x 1e7 = 240 MB)",
-                   "parallelism": f"{ws} independent reconstructions" if ws > 1 else "1 GPU"},
+                   "parallelism": (f"one reconstruction, events sharded over {ws} GPUs, NCCL "
+                                   f"all-reduce of the back-projection each iteration"
+                                   if ws > 1 else "1 GPU")},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "batched": batched,
-        "adjoint": adjoint,
+        "adjoint": adjoint, "stress": stress,
         "gpu_launches": launches,
         "clocks": clk,
-        "checks": {"conservation_rel": cons, "n_used": st1["n_used"],
+        "checks": {"conservation_rel": cons, "n_used": used,
                    "n_outliers": st1["n_outliers"], "n_empty": st1["n_empty"]},
     }
     print(json.dumps(line), flush=True)

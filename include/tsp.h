@@ -27,6 +27,14 @@
  *    the caller.  Distinct contexts are independent.
  *  - The library owns all device memory it allocates and frees it in
  *    tsp_destroy().
+ *  - Error paths can be exercised without a device fault: the environment
+ *    variable TSP_SIM_FAULT = oom (device allocations fail: TSP_ENOMEM),
+ *    launch (kernel launches fail before anything is enqueued: TSP_ECUDA) or
+ *    nan_event (each uploaded chunk gets a NaN z_u: TSP_EINVAL) simulates that
+ *    failure at every site it reaches while it is set.  A context whose call
+ *    failed this way can still be destroyed, and new contexts work once the
+ *    variable is unset.
+ *  - Each entry point that enqueues work opens an NVTX range of its name.
  */
 #ifndef TSP_H
 #define TSP_H
@@ -143,6 +151,40 @@ int tsp_set_image(tsp_ctx* ctx, const float* rho, int on_device, void* stream);
  * graph captured on the first call with this n_iter.  Requires an upload
  * (TSP_ESTATE otherwise).  Asynchronous on stream. */
 int tsp_iterate(tsp_ctx* ctx, int n_iter, void* stream);
+
+/* Event-sharded iteration.  Eq. iter is a sum over events, and given the
+ * image rho^t the events are independent: an update over a list split into
+ * shards (one context per shard, e.g. one per GPU, every context holding the
+ * same image) is the update over the whole list when the shards'
+ * back-projections are summed before the image is multiplied.
+ *
+ * tsp_backproject writes the back-projection of this context's events at the
+ * current image,
+ *   A_out[l] = sum_j P(e_j|l) / D_j,   D_j = sum_i P(e_j|i) s_i rho_i,
+ * over the events with D_j > 0 (ny*nz floats, host or device per on_device),
+ * with the kernel P of Eq. kernel (Sec. 3) over each event's window.  The
+ * image is not changed; tsp_stats then reports the events used.  Requires an
+ * upload (TSP_ESTATE; an empty list gives A = 0).  A host A_out is filled when
+ * the call returns; a device A_out is written asynchronously on stream.
+ *
+ * tsp_apply_update applies rho_l <- rho_l * A[l] (the last step of Eq. iter)
+ * with A given by the caller (ny*nz floats, host or device), typically the sum
+ * of every shard's back-projection (an all-reduce); it refreshes rho' = s rho
+ * and the sum of s rho and advances the iteration counter by one.  Host
+ * values must be finite and >= 0 (TSP_EINVAL, nothing applied); device data
+ * is not checked.
+ *
+ * One context's tsp_backproject followed by tsp_apply_update of its own A is
+ * one tsp_iterate(ctx, 1) step up to float rounding order. */
+int tsp_backproject(tsp_ctx* ctx, float* A_out, int on_device, void* stream);
+int tsp_apply_update(tsp_ctx* ctx, const float* A, int on_device, void* stream);
+
+/* Bounded wait (no counterpart in the paper): wait on the host until the work
+ * enqueued on stream so far has finished, for at most timeout_ms >= 0
+ * milliseconds.  Returns 0 when it has finished, TSP_ETIMEOUT when the limit
+ * ran out first (the work continues; the context stays usable and the call
+ * may be repeated), TSP_ECUDA when the stream reports an error. */
+int tsp_wait(tsp_ctx* ctx, void* stream, int timeout_ms);
 
 /* Direct-reconstruction image (Eq. 2, Sec. 2): out[iy*nz + iz] = the number of
  * uploaded events whose point (y~, z~) lies in pixel (iy, iz), i.e. y~ in

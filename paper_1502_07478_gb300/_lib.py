@@ -63,6 +63,9 @@ SIGNATURES = [
     ("tsp_iterate", C.c_int, [_vp, C.c_int, _vp]),
     ("tsp_read_image", C.c_int, [_vp, _fp, C.c_int, C.c_int, _vp]),
     ("tsp_direct_image", C.c_int, [_vp, _fp, C.c_int, _vp]),
+    ("tsp_backproject", C.c_int, [_vp, _fp, C.c_int, _vp]),
+    ("tsp_apply_update", C.c_int, [_vp, _fp, C.c_int, _vp]),
+    ("tsp_wait", C.c_int, [_vp, _vp, C.c_int]),
     ("tsp_loglik", C.c_int, [_vp, C.POINTER(C.c_double), _vp]),
     ("tsp_loglik_grad", C.c_int, [_vp, C.POINTER(C.c_double), _fp, C.c_int,
                                   C.POINTER(C.c_double), _vp]),

@@ -6,11 +6,14 @@
 // Eq. iter.  Every entry point validates its arguments, runs on the context's
 // device, and reports failures through return codes and tsp_last_error().
 #include <algorithm>
+#include <chrono>
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "tsp_ctx.h"
@@ -79,33 +82,19 @@ int plan(tsp_ctx* c)
     const double cut = p.cut > 0 ? p.cut : 3.0;
     c->g = make_geo(p);
 
-    // lane capacity: the longest chord of the ellipse is 2 cut sigma_z / sqrt(2),
-    // with the largest sigma_z of any event, sigma_z (1 + kappa_z)
+    // lane capacity, row split, rows per window and warps per event (shared
+    // with the allocation-free entry point)
+    LanePlan lp;
+    if (const char* why = lane_plan(p, lp)) return fail(c, TSP_EINVAL, why);
+    c->lmax = lp.lmax;
+    c->nseg = lp.nseg;
+    c->need = lp.need;
+    c->maxrows = lp.maxrows;
+    c->G = lp.G;
+    const int need = lp.need, maxrows = lp.maxrows;
     const double szmax = p.sigma_z * (1.0 + p.kappa_z);
     const double umax = cut * szmax / std::sqrt(2.0);
-    const int need = (int)std::floor(2.0 * umax / dz) + 2;
-    // one lane per row (whole chord), or two lanes per row (one per half)
-    int best_l = 0, best_s = 0;
-    for (int k = 0; k < kLmaxCount && !best_l; ++k)
-        if (kLmaxList[k] >= need) {
-            best_l = kLmaxList[k];
-            best_s = 1;
-        }
-    for (int k = 0; k < kLmaxCount && !best_l; ++k)
-        if (kLmaxList[k] >= need / 2 + 2) {
-            best_l = kLmaxList[k];
-            best_s = 2;
-        }
-    if (!best_l) return fail(c, TSP_EINVAL, "window chords too long for the compiled lane capacities");
-    c->lmax = best_l;
-    c->nseg = best_s;
-    c->need = need;
-    // rows of a window: |Dy| <= cut sigma_dl cos / 2
     const double hy = cut * p.sigma_dl / 2.0 * 1.00001;
-    const int maxrows = (int)std::floor(2.0 * hy / dy) + 2;
-    c->maxrows = maxrows;
-    c->G = c->nseg * ((maxrows + 31) / 32);
-    if (c->G > kMinWarps) return fail(c, TSP_EINVAL, "window has more rows than one block can hold");
 
     // tiling (see Tiling): angle bins of width 1/16 in tan(theta~) cover the
     // accepted range |t| <= L/2R widened by 6 sigma of its measurement noise
@@ -152,9 +141,7 @@ int plan(tsp_ctx* c)
             TY -= 4;
         if (tiles_acc_smem_floats(TY + 2 * tl.HY, RS) * sizeof(float) <= budget) {
             c->gld = 1;
-            int l2 = 0;
-            for (int k = 0; k < kLmaxCount && !l2; ++k)
-                if (kLmaxList[k] >= need / 2 + 2) l2 = kLmaxList[k];
+            const int l2 = lane_lmax_split(need);
             if (!l2) return fail(c, TSP_EINVAL, "window chords too long for the lane capacities");
             c->lmax = l2;
             c->nseg = 2;
@@ -260,9 +247,9 @@ int prep_begin(tsp_ctx* c, cudaStream_t st)
     dfree(c->bin_count);
     dfree(c->offsets);
     dfree(c->cursor);
-    TSP_CUDA(c, cudaMalloc(&c->bin_count, sizeof(int) * nbins));
-    TSP_CUDA(c, cudaMalloc(&c->offsets, sizeof(long long) * nbins));
-    TSP_CUDA(c, cudaMalloc(&c->cursor, sizeof(int) * nbins));
+    TSP_CUDA(c, dmalloc(&c->bin_count, sizeof(int) * nbins));
+    TSP_CUDA(c, dmalloc(&c->offsets, sizeof(long long) * nbins));
+    TSP_CUDA(c, dmalloc(&c->cursor, sizeof(int) * nbins));
     TSP_CUDA(c, cudaMemsetAsync(c->bin_count, 0, sizeof(int) * nbins, st));
     TSP_CUDA(c, cudaMemsetAsync(c->cursor, 0, sizeof(int) * nbins, st));
     TSP_CUDA(c, cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * 4, st));
@@ -311,7 +298,7 @@ int prep_finish(tsp_ctx* c, cudaStream_t st)
     c->n_items = (int)items.size();
     if (c->n_items > c->items_cap) {
         dfree(c->items);
-        TSP_CUDA(c, cudaMalloc(&c->items, sizeof(int4) * std::max(1, c->n_items)));
+        TSP_CUDA(c, dmalloc(&c->items, sizeof(int4) * std::max(1, c->n_items)));
         c->items_cap = c->n_items;
     }
     if (c->n_items)
@@ -374,16 +361,16 @@ int ensure_event_capacity(tsp_ctx* c, long long n)
     dfree(c->rows);
     dfree(c->key);
     c->cap = 0;
-    TSP_CUDA(c, cudaMalloc(&c->zu, sizeof(float) * n));
-    TSP_CUDA(c, cudaMalloc(&c->zd, sizeof(float) * n));
-    TSP_CUDA(c, cudaMalloc(&c->dl, sizeof(float) * n));
-    TSP_CUDA(c, cudaMalloc(&c->geo_u, sizeof(float4) * n));
-    TSP_CUDA(c, cudaMalloc(&c->geo, sizeof(float4) * n));
-    TSP_CUDA(c, cudaMalloc(&c->geo64_u, sizeof(Ev64) * n));
-    TSP_CUDA(c, cudaMalloc(&c->geo64, sizeof(Ev64) * n));
-    TSP_CUDA(c, cudaMalloc(&c->rows_u, sizeof(int2) * n));
-    TSP_CUDA(c, cudaMalloc(&c->rows, sizeof(int2) * n));
-    TSP_CUDA(c, cudaMalloc(&c->key, sizeof(int) * n));
+    TSP_CUDA(c, dmalloc(&c->zu, sizeof(float) * n));
+    TSP_CUDA(c, dmalloc(&c->zd, sizeof(float) * n));
+    TSP_CUDA(c, dmalloc(&c->dl, sizeof(float) * n));
+    TSP_CUDA(c, dmalloc(&c->geo_u, sizeof(float4) * n));
+    TSP_CUDA(c, dmalloc(&c->geo, sizeof(float4) * n));
+    TSP_CUDA(c, dmalloc(&c->geo64_u, sizeof(Ev64) * n));
+    TSP_CUDA(c, dmalloc(&c->geo64, sizeof(Ev64) * n));
+    TSP_CUDA(c, dmalloc(&c->rows_u, sizeof(int2) * n));
+    TSP_CUDA(c, dmalloc(&c->rows, sizeof(int2) * n));
+    TSP_CUDA(c, dmalloc(&c->key, sizeof(int) * n));
     c->cap = n;
     return TSP_OK;
 }
@@ -468,23 +455,30 @@ int tsp_create(const tsp_params* params, tsp_ctx** out)
         c->err = "no CUDA device";
         return bail(TSP_ECUDA);
     }
-    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev);
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev) !=
+            cudaSuccess ||
+        c->num_sms <= 0) {
+        cudaGetLastError();
+        c->err = "cudaDeviceGetAttribute(MultiProcessorCount) failed";
+        return bail(TSP_ECUDA);
+    }
     if ((rc = plan(c))) return bail(rc);
     c->npix = params->ny * params->nz;
     const size_t img = sizeof(float) * (size_t)c->npix;
     const size_t padded = img + sizeof(float) * kPadFloats;
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&c->rho, img);
-    if (e == cudaSuccess) e = cudaMalloc(&c->rhop, padded);
-    if (e == cudaSuccess) e = cudaMalloc(&c->A, padded);
-    if (e == cudaSuccess) e = cudaMalloc(&c->s, img);
-    if (e == cudaSuccess) e = cudaMalloc(&c->gbuf, img);
-    if (e == cudaSuccess) e = cudaMalloc(&c->accum, sizeof(Accum));
-    if (e == cudaSuccess) e = cudaMalloc(&c->counters, sizeof(unsigned long long) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&c->flag, sizeof(int));
+    if (e == cudaSuccess) e = dmalloc(&c->rho, img);
+    if (e == cudaSuccess) e = dmalloc(&c->rhop, padded);
+    if (e == cudaSuccess) e = dmalloc(&c->A, padded);
+    if (e == cudaSuccess) e = dmalloc(&c->s, img);
+    if (e == cudaSuccess) e = dmalloc(&c->gbuf, img);
+    if (e == cudaSuccess) e = dmalloc(&c->accum, sizeof(Accum));
+    if (e == cudaSuccess) e = dmalloc(&c->counters, sizeof(unsigned long long) * 4);
+    if (e == cudaSuccess) e = dmalloc(&c->flag, sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->copy_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->wait_ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(c->rhop, 0, padded);
     if (e == cudaSuccess) e = cudaMemset(c->A, 0, padded);
     if (e == cudaSuccess) e = cudaMemset(c->accum, 0, sizeof(Accum));
@@ -507,6 +501,7 @@ void tsp_destroy(tsp_ctx* c)
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->copy_ev) cudaEventDestroy(c->copy_ev);
+    if (c->wait_ev) cudaEventDestroy(c->wait_ev);
     dfree(c->rho); dfree(c->rhop); dfree(c->A); dfree(c->s); dfree(c->gbuf);
     dfree(c->accum); dfree(c->counters); dfree(c->flag);
     dfree(c->zu); dfree(c->zd); dfree(c->dl);
@@ -518,6 +513,7 @@ void tsp_destroy(tsp_ctx* c)
 
 int tsp_begin_events(tsp_ctx* c, int64_t n_total, void* stream)
 {
+    NvtxRange nvtx_("tsp_begin_events");
     if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
     if (n_total < 0) return fail(c, TSP_EINVAL, "n_total < 0");
     if (n_total > (1ll << 31) - 1) return fail(c, TSP_EINVAL, "more than 2^31-1 events");
@@ -542,6 +538,7 @@ int tsp_begin_events(tsp_ctx* c, int64_t n_total, void* stream)
 int tsp_append_events(tsp_ctx* c, const float* zu, const float* zd, const float* dl, int64_t n,
                       int on_device, void* stream)
 {
+    NvtxRange nvtx_("tsp_append_events");
     if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
     if (!c->appending) return fail(c, TSP_ESTATE, "append_events without begin_events");
     if (n < 0) return fail(c, TSP_EINVAL, "n < 0");
@@ -562,6 +559,8 @@ int tsp_append_events(tsp_ctx* c, const float* zu, const float* zd, const float*
         TSP_CUDA(c, cudaEventRecord(c->copy_ev, cs));
         TSP_CUDA(c, cudaStreamWaitEvent(st, c->copy_ev, 0));
     }
+    if (sim_fault() == kSimNan)   // simulated corrupt input: a NaN in the first z_u
+        TSP_CUDA(c, cudaMemsetAsync(c->zu + first, 0xff, sizeof(float), st));
     if ((rc = prep_chunk(c, first, n, st))) return rc;
     c->n = first + n;
     return TSP_OK;
@@ -569,6 +568,7 @@ int tsp_append_events(tsp_ctx* c, const float* zu, const float* zd, const float*
 
 int tsp_end_events(tsp_ctx* c, void* stream)
 {
+    NvtxRange nvtx_("tsp_end_events (binning)");
     if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
     if (!c->appending) return fail(c, TSP_ESTATE, "end_events without begin_events");
     DeviceGuard dg(c->dev);
@@ -587,6 +587,7 @@ int tsp_end_events(tsp_ctx* c, void* stream)
 int tsp_upload_events(tsp_ctx* c, const float* zu, const float* zd, const float* dl, int64_t n,
                       int on_device, void* stream)
 {
+    NvtxRange nvtx_("tsp_upload_events");
     if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
     if (n < 0) return fail(c, TSP_EINVAL, "n < 0");
     if (n > 0 && (!zu || !zd || !dl)) return fail(c, TSP_EINVAL, "event pointer is NULL");
@@ -598,6 +599,7 @@ int tsp_upload_events(tsp_ctx* c, const float* zu, const float* zd, const float*
 
 int tsp_compute_sensitivity(tsp_ctx* c, float* out, int on_device, void* stream)
 {
+    NvtxRange nvtx_("tsp_compute_sensitivity");
     if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
     DeviceGuard dg(c->dev);
     cudaStream_t st = (cudaStream_t)stream;
@@ -612,6 +614,7 @@ int tsp_compute_sensitivity(tsp_ctx* c, float* out, int on_device, void* stream)
 
 int tsp_set_image(tsp_ctx* c, const float* rho, int on_device, void* stream)
 {
+    NvtxRange nvtx_("tsp_set_image");
     if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
     DeviceGuard dg(c->dev);
     cudaStream_t st = (cudaStream_t)stream;
@@ -643,6 +646,7 @@ int tsp_set_image(tsp_ctx* c, const float* rho, int on_device, void* stream)
 
 int tsp_iterate(tsp_ctx* c, int n_iter, void* stream)
 {
+    NvtxRange nvtx_("tsp_iterate");
     if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
     if (n_iter < 0) return fail(c, TSP_EINVAL, "n_iter < 0");
     if (!c->uploaded) return fail(c, TSP_ESTATE, "iterate before upload_events");
@@ -665,6 +669,7 @@ int tsp_iterate(tsp_ctx* c, int n_iter, void* stream)
 
 int tsp_read_image(tsp_ctx* c, float* out, int which, int on_device, void* stream)
 {
+    NvtxRange nvtx_("tsp_read_image");
     if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
     if (!out) return fail(c, TSP_EINVAL, "out is NULL");
     if (which != 0 && which != 1) return fail(c, TSP_EINVAL, "which must be 0 (rho) or 1 (rho')");
@@ -684,6 +689,7 @@ int tsp_loglik(tsp_ctx* c, double* out, void* stream)
 int tsp_loglik_grad(tsp_ctx* c, double* L_out, float* g_rho, int g_on_device, double* g_sigma,
                     void* stream)
 {
+    NvtxRange nvtx_("tsp_loglik_grad");
     if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
     if (!c->uploaded) return fail(c, TSP_ESTATE, "loglik before upload_events");
     DeviceGuard dg(c->dev);
@@ -914,6 +920,74 @@ int tsp_autotune(tsp_ctx* c, tsp_schedule* chosen, float* best_ms, void* stream)
     if (chosen) *chosen = best;
     if (best_ms) *best_ms = best_t;
     return TSP_OK;
+}
+
+int tsp_backproject(tsp_ctx* c, float* A_out, int on_device, void* stream)
+{
+    NvtxRange nvtx_("tsp_backproject");
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (!A_out) return fail(c, TSP_EINVAL, "A_out is NULL");
+    if (!c->uploaded) return fail(c, TSP_ESTATE, "backproject before upload_events");
+    DeviceGuard dg(c->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = refresh_rhop(c, st);   // clears the pass counters, rho' = s rho, sum s rho
+    if (rc) return rc;
+    const PassArgs a = pass_args(c);
+    TSP_CUDA(c, launch_mlem_pass(c, a, st));
+    c->launches += mlem_pass_launches(c);
+    if ((rc = copy_floats(c, A_out, c->A, c->npix, on_device, 1, st))) return rc;
+    // A is zero between passes (the next pass accumulates into it)
+    TSP_CUDA(c, cudaMemsetAsync(c->A, 0, sizeof(float) * c->npix, st));
+    if (!on_device) TSP_CUDA(c, cudaStreamSynchronize(st));
+    return TSP_OK;
+}
+
+int tsp_apply_update(tsp_ctx* c, const float* A, int on_device, void* stream)
+{
+    NvtxRange nvtx_("tsp_apply_update");
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (!A) return fail(c, TSP_EINVAL, "A is NULL");
+    if (c->appending) return fail(c, TSP_ESTATE, "apply_update between begin_events and end_events");
+    if (!on_device)
+        for (int i = 0; i < c->npix; ++i)
+            if (!(std::isfinite(A[i]) && A[i] >= 0.0f))
+                return fail(c, TSP_EINVAL, "A must be finite and >= 0");
+    DeviceGuard dg(c->dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_sensitivity(c, st);
+    if (rc) return rc;
+    if ((rc = copy_floats(c, c->A, A, c->npix, 1, on_device, st))) return rc;
+    // sum s rho is accumulated afresh by the update; the counters of the last
+    // back-projection (events used) are kept
+    TSP_CUDA(c, cudaMemsetAsync(reinterpret_cast<char*>(c->accum) + offsetof(Accum, sum_rhop), 0,
+                                sizeof(double), st));
+    TSP_CUDA(c, launch_finalize(c->npix, c->rho, c->rhop, c->A, c->s, c->accum, st));
+    c->launches += 1;
+    c->iterations += 1;
+    if (!on_device) TSP_CUDA(c, cudaStreamSynchronize(st));
+    return TSP_OK;
+}
+
+int tsp_wait(tsp_ctx* c, void* stream, int timeout_ms)
+{
+    if (!c) return fail(nullptr, TSP_EINVAL, "ctx is NULL");
+    if (timeout_ms < 0) return fail(c, TSP_EINVAL, "timeout_ms < 0");
+    DeviceGuard dg(c->dev);
+    TSP_CUDA(c, cudaEventRecord(c->wait_ev, (cudaStream_t)stream));
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(c->wait_ev);
+        if (e == cudaSuccess) return TSP_OK;
+        if (e != cudaErrorNotReady)
+            return fail(c, TSP_ECUDA, std::string("cudaEventQuery: ") + cudaGetErrorString(e));
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                            std::chrono::steady_clock::now() - t0)
+                            .count();
+        if (ms >= timeout_ms)
+            return fail(c, TSP_ETIMEOUT, "the work enqueued on the stream did not finish within " +
+                                             std::to_string(timeout_ms) + " ms");
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
 }
 
 int tsp_pass_times(tsp_ctx* c, float* ms, int max, int* count, void* stream)

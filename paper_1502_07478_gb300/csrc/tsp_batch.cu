@@ -226,12 +226,12 @@ int rebuild(tsp_batch* b, cudaStream_t st)
         BATCH_CUDA(b, prepare_batch_pass(bc.lmax, limit));
         if ((int)items.size() > bc.items_cap) {
             dfree(bc.items);
-            BATCH_CUDA(b, cudaMalloc(&bc.items, sizeof(int4) * items.size()));
+            BATCH_CUDA(b, dmalloc(&bc.items, sizeof(int4) * items.size()));
             bc.items_cap = (int)items.size();
         }
         if ((int)outl.size() > bc.oitems_cap) {
             dfree(bc.oitems);
-            BATCH_CUDA(b, cudaMalloc(&bc.oitems, sizeof(int4) * outl.size()));
+            BATCH_CUDA(b, dmalloc(&bc.oitems, sizeof(int4) * outl.size()));
             bc.oitems_cap = (int)outl.size();
         }
         if (!items.empty())
@@ -416,7 +416,13 @@ int tsp_batch_create(const tsp_params* params, int k, tsp_batch** out)
         b->err = "no CUDA device";
         return bail(TSP_ECUDA);
     }
-    cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->dev);
+    if (cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->dev) !=
+            cudaSuccess ||
+        b->num_sms <= 0) {
+        cudaGetLastError();
+        b->err = "cudaDeviceGetAttribute(MultiProcessorCount) failed";
+        return bail(TSP_ECUDA);
+    }
     b->inst.reserve(k);
     for (int i = 0; i < k; ++i) {
         tsp_ctx* c = nullptr;
@@ -428,9 +434,9 @@ int tsp_batch_create(const tsp_params* params, int k, tsp_batch** out)
         b->inst.push_back(c);
         c->sched = b->sched;
     }
-    cudaError_t e = cudaMalloc(&b->table, sizeof(Inst) * k);
-    if (e == cudaSuccess) e = cudaMalloc(&b->imgs, sizeof(BatchImg) * k);
-    if (e == cudaSuccess) e = cudaMalloc(&b->queue, sizeof(int) * kMaxClasses);
+    cudaError_t e = dmalloc(&b->table, sizeof(Inst) * k);
+    if (e == cudaSuccess) e = dmalloc(&b->imgs, sizeof(BatchImg) * k);
+    if (e == cudaSuccess) e = dmalloc(&b->queue, sizeof(int) * kMaxClasses);
     if (e == cudaSuccess) e = cudaMemset(b->queue, 0, sizeof(int) * kMaxClasses);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -464,6 +470,7 @@ int tsp_batch_size(const tsp_batch* b) { return b ? (int)b->inst.size() : 0; }
 int tsp_batch_upload_events(tsp_batch* b, int i, const float* zu, const float* zd,
                             const float* dl, int64_t n, int on_device, void* stream)
 {
+    NvtxRange nvtx_("tsp_batch_upload_events");
     int rc = check_index(b, i);
     if (rc) return rc;
     b->dirty = true;
@@ -491,6 +498,7 @@ int tsp_batch_set_sigma(tsp_batch* b, int i, double sigma_z, double sigma_dl, vo
 
 int tsp_batch_iterate(tsp_batch* b, int n_iter, void* stream)
 {
+    NvtxRange nvtx_("tsp_batch_iterate");
     if (!b) return bfail(nullptr, TSP_EINVAL, "batch is NULL");
     if (n_iter < 0) return bfail(b, TSP_EINVAL, "n_iter < 0");
     DeviceGuard dg(b->dev);
@@ -513,6 +521,7 @@ int tsp_batch_iterate(tsp_batch* b, int n_iter, void* stream)
 
 int tsp_batch_read_image(tsp_batch* b, int i, float* out, int which, int on_device, void* stream)
 {
+    NvtxRange nvtx_("tsp_batch_read_image");
     int rc = check_index(b, i);
     if (rc) return rc;
     if (which == 2) {
@@ -534,6 +543,7 @@ int tsp_batch_read_image(tsp_batch* b, int i, float* out, int which, int on_devi
 
 int tsp_batch_loglik_grad(tsp_batch* b, double* L_out, double* g_sigma, void* stream)
 {
+    NvtxRange nvtx_("tsp_batch_loglik_grad");
     if (!b) return bfail(nullptr, TSP_EINVAL, "batch is NULL");
     DeviceGuard dg(b->dev);
     cudaStream_t st = (cudaStream_t)stream;

@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "tsp.h"
 #include "tsp_launch.h"
 
@@ -73,6 +75,7 @@ struct tsp_ctx {
     long long n_total = 0;            // events declared by tsp_begin_events
     cudaStream_t copy_stream = nullptr;   // host-to-device event copies
     cudaEvent_t copy_ev = nullptr;
+    cudaEvent_t wait_ev = nullptr;        // tsp_wait's completion marker
     long long iterations = 0;
     cudaStream_t cap_stream = nullptr;
     struct Graph {
@@ -100,6 +103,15 @@ struct DeviceGuard {
     {
         if (prev >= 0) cudaSetDevice(prev);
     }
+};
+
+// An NVTX range around one entry point (upload, binning, iteration, readout),
+// for timelines taken with a profiler; free when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // Record msg as the context's last error (or the creation error when c is

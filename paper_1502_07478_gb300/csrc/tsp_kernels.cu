@@ -1,6 +1,8 @@
 // Auxiliary kernels of libtsp: sensitivity (Eq. s-yz), per-event preparation
 // (Eq. 2 and the App. B window), binning of events by image tile, the image
 // update that closes one iteration of Eq. iter, and small reductions.
+#include <cstdlib>
+#include <cstring>
 #include <climits>
 #include <cmath>
 
@@ -420,6 +422,16 @@ Geo make_geo(const tsp_params& p)
     return g;
 }
 
+int sim_fault()
+{
+    const char* v = std::getenv("TSP_SIM_FAULT");
+    if (!v) return kSimNone;
+    if (!std::strcmp(v, "oom")) return kSimOom;
+    if (!std::strcmp(v, "launch")) return kSimLaunch;
+    if (!std::strcmp(v, "nan_event")) return kSimNan;
+    return kSimNone;
+}
+
 cudaError_t launch_sensitivity(double R, double L, int ny, int nz, double dy, double dz, float* s,
                                cudaStream_t st)
 {
@@ -433,6 +445,7 @@ cudaError_t launch_setup(const Geo& g, const Tiling& tl, long long n, const floa
                          int* key, unsigned long long* counters, int* bin_count, int nbins,
                          cudaStream_t st)
 {
+    if (cudaError_t f = sim_launch()) return f;
     if (n <= 0) return cudaSuccess;
     const size_t smem = nbins <= 8192 ? (size_t)nbins * sizeof(int) : 0;
     k_setup<<<blocks_for(n, kAuxThreads * 8, 4096), kAuxThreads, smem, st>>>(
@@ -460,6 +473,7 @@ cudaError_t launch_scatter(long long n, int nbins, const int* key, const float4*
 
 cudaError_t launch_begin(Accum* accum, cudaStream_t st)
 {
+    if (cudaError_t f = sim_launch()) return f;
     k_begin<<<1, 32, 0, st>>>(accum);
     return cudaGetLastError();
 }
@@ -467,6 +481,7 @@ cudaError_t launch_begin(Accum* accum, cudaStream_t st)
 cudaError_t launch_finalize(int npix, float* rho, float* rhop, float* A, const float* s,
                             Accum* accum, cudaStream_t st)
 {
+    if (cudaError_t f = sim_launch()) return f;
     k_finalize<<<blocks_for(npix, kAuxThreads * 4, 1024), kAuxThreads, 0, st>>>(npix, rho, rhop, A,
                                                                                s, accum);
     return cudaGetLastError();
@@ -474,6 +489,7 @@ cudaError_t launch_finalize(int npix, float* rho, float* rhop, float* A, const f
 
 cudaError_t launch_grad_finalize(int npix, float* g, float* A, const float* s, cudaStream_t st)
 {
+    if (cudaError_t f = sim_launch()) return f;
     k_grad_finalize<<<blocks_for(npix, kAuxThreads * 4, 1024), kAuxThreads, 0, st>>>(npix, g, A, s);
     return cudaGetLastError();
 }
@@ -481,6 +497,7 @@ cudaError_t launch_grad_finalize(int npix, float* g, float* A, const float* s, c
 cudaError_t launch_set_rhop(int npix, const float* rho, const float* s, float* rhop, Accum* accum,
                             cudaStream_t st)
 {
+    if (cudaError_t f = sim_launch()) return f;
     k_set_rhop<<<blocks_for(npix, kAuxThreads * 4, 1024), kAuxThreads, 0, st>>>(npix, rho, s, rhop,
                                                                                accum);
     return cudaGetLastError();
@@ -515,12 +532,14 @@ cudaError_t launch_check_image(int n, const float* rho, int* bad, cudaStream_t s
 
 cudaError_t launch_batch_begin(const BatchImg* im, int k, int* queue, int nq, cudaStream_t st)
 {
+    if (cudaError_t f = sim_launch()) return f;
     k_batch_begin<<<1, kAuxThreads, 0, st>>>(im, k, queue, nq);
     return cudaGetLastError();
 }
 
 cudaError_t launch_batch_pixels(const BatchImg* im, int k, int max_npix, int op, cudaStream_t st)
 {
+    if (cudaError_t f = sim_launch()) return f;
     if (k <= 0) return cudaSuccess;
     const dim3 grid(blocks_for(max_npix, kAuxThreads * 4, 256), k);
     k_batch_pixels<<<grid, kAuxThreads, 0, st>>>(im, op);
@@ -529,6 +548,7 @@ cudaError_t launch_batch_pixels(const BatchImg* im, int k, int max_npix, int op,
 
 cudaError_t launch_batch_pass(int lmax, int mode, const BatchArgs& a, cudaStream_t st)
 {
+    if (cudaError_t f = sim_launch()) return f;
     switch (lmax) {
     case 12: return launch_batch_pass_l<12>(mode, a, st);
     case 24: return launch_batch_pass_l<24>(mode, a, st);
@@ -551,6 +571,7 @@ cudaError_t prepare_batch_pass(int lmax, size_t smem)
 
 cudaError_t launch_pass(int lmax, int mode, const PassArgs& a, cudaStream_t st)
 {
+    if (cudaError_t f = sim_launch()) return f;
     switch (lmax) {
     case 12: return launch_pass_l<12>(mode, a, st);
     case 24: return launch_pass_l<24>(mode, a, st);

@@ -78,6 +78,7 @@ k_thread_events(Geo g, EventsView evs, int n, const float* __restrict__ rhop,
 cudaError_t launch_thread_pass(const Geo& g, const EventsView& evs, int n, const float* rhop,
                                float* A, Accum* accum, int sms, cudaStream_t st)
 {
+    if (cudaError_t f = sim_launch()) return f;
     if (n <= 0) return cudaSuccess;
     int blocks = (n + kThreadBlock - 1) / kThreadBlock;
     if (blocks > 8 * sms) blocks = 8 * sms;

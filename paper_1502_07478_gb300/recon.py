@@ -164,6 +164,42 @@ class Recon:
         self._chk(self._lib.tsp_read_image(self._h, p, int(which), dev, _stream_handle(stream)))
         return out
 
+    def backproject(self, out=None, stream=None):
+        """Back-projection of this reconstruction's events at the current image
+        (tsp_backproject): A[l] = sum_j P(e_j|l) / D_j, as a CUDA tensor or into
+        ``out`` (a CUDA tensor or a NumPy array).  The image is unchanged."""
+        if out is None:
+            out = torch.empty(self.ny, self.nz, dtype=torch.float32, device="cuda")
+        if isinstance(out, np.ndarray):
+            if out.dtype != np.float32 or not out.flags.c_contiguous or out.size != self.ny * self.nz:
+                raise ValueError("out must be a contiguous float32 array of ny*nz elements")
+            self._chk(self._lib.tsp_backproject(self._h, C.c_void_p(out.ctypes.data), 0,
+                                                _stream_handle(stream)))
+            return out
+        p, dev, keep = _arg(out)
+        if keep is not out:
+            raise ValueError("out must be a contiguous float32 CUDA tensor")
+        self._chk(self._lib.tsp_backproject(self._h, p, dev, _stream_handle(stream)))
+        return out
+
+    def apply_update(self, A, stream=None):
+        """rho <- rho * A (tsp_apply_update), A a CUDA tensor or host array of
+        ny*nz floats, e.g. the sum of every shard's back-projection."""
+        p, dev, keep = _arg(A)
+        size = keep.numel() if dev else keep.size
+        if size != self.ny * self.nz:
+            raise ValueError("A must have ny*nz elements")
+        self._chk(self._lib.tsp_apply_update(self._h, p, dev, _stream_handle(stream)))
+
+    def wait(self, timeout_ms: int, stream=None) -> bool:
+        """Wait up to timeout_ms for the work enqueued on the stream
+        (tsp_wait): True when it finished, False when the limit ran out."""
+        rc = self._lib.tsp_wait(self._h, _stream_handle(stream), int(timeout_ms))
+        if rc == L.TSP_ETIMEOUT:
+            return False
+        self._chk(rc)
+        return True
+
     def direct_image(self, out=None, stream=None):
         """Counts of the events' direct reconstructions (Eq. 2) per pixel, as a
         CUDA tensor or into ``out`` (CUDA tensor or NumPy array)."""

@@ -1,0 +1,173 @@
+"""Event-sharded iteration through the C ABI (tsp_backproject, tsp_apply_update)
+on one GPU: the shards are separate contexts holding disjoint parts of the
+event list, their back-projections are summed (the all-reduce of a multi-GPU
+run), and every shard applies the sum.
+
+Eq. iter is a sum over events, so the sharded iteration must equal the
+iteration over the whole list: against one context over all events up to the
+float summation order (ORDER_TOL), and against the FP64 oracle at the parity
+bar (max relative error <= 1e-4 on pixels above 1% of the maximum).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Setup
+from synth import make_workload
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+# Shards change only the order in which the same FP32 contributions are summed
+# (two partial sums per pixel instead of one), the same effect as the
+# nondeterministic order of the float atomics between two runs of one context.
+ORDER_TOL = 2e-5
+
+
+def rel_err(a, b, frac=0.01):
+    a = np.asarray(a, np.float64).reshape(b.shape)
+    b = np.asarray(b, np.float64)
+    m = b > frac * b.max()
+    return float(np.max(np.abs(a[m] - b[m]) / b[m]))
+
+
+def _recon(w):
+    from paper_1502_07478_gb300 import Recon
+    return Recon.from_workload(w)
+
+
+def _sharded(w, ev, k, n_iter):
+    """k contexts on interleaved shares of the events; n_iter sharded iterations."""
+    import torch
+    shards = []
+    for r in range(k):
+        c = _recon(w)
+        c.upload_events(*[e[r::k] for e in ev])
+        shards.append(c)
+    bufs = [torch.empty(w.ny, w.nz, dtype=torch.float32, device="cuda") for _ in range(k)]
+    for _ in range(n_iter):
+        for c, b in zip(shards, bufs):
+            c.backproject(out=b)
+        total = torch.stack(bufs).sum(0)
+        for c in shards:
+            c.apply_update(total)
+    imgs = [c.read_image().cpu().numpy() for c in shards]
+    used = sum(c.stats()["n_used"] for c in shards)
+    sums = [c.stats()["sum_s_rho"] for c in shards]
+    iters = [c.stats()["iterations"] for c in shards]
+    for c in shards:
+        c.close()
+    return imgs, used, sums, iters
+
+
+def test_sharded_equals_whole_and_oracle():
+    """small 5 mm workload, 2 shards, 5 iterations."""
+    w = make_workload("small_5mm")
+    ev = w.events()
+    imgs, used, sums, iters = _sharded(w, ev, 2, 5)
+    np.testing.assert_array_equal(imgs[0], imgs[1])     # identical updates on every shard
+    assert iters == [5, 5]
+    r = _recon(w)
+    r.upload_events(*ev)
+    r.iterate(5)
+    whole = r.read_image().cpu().numpy()
+    st = r.stats()
+    r.close()
+    assert rel_err(imgs[0], whole) <= ORDER_TOL
+    ref, rst = oracle.mlem(Setup.from_workload(w), ev, 5)
+    assert rel_err(imgs[0], ref) <= TOL
+    assert used == rst.n_used == st["n_used"]
+    # count conservation: sum_l s_l rho_l = N_used over all shards
+    assert sums[0] == pytest.approx(rst.n_used, rel=2e-6)
+
+
+def test_sharded_paper_1mm_subset_four_shards():
+    """1 mm grid (the paper-scale geometry), 1e5 events in 4 uneven shards
+    (contiguous runs of different lengths), 3 iterations, against one context."""
+    import torch
+    w = make_workload("paper_1mm", n_events=100_000)
+    ev = w.events()
+    cuts = [0, 10_000, 35_000, 70_000, 100_000]
+    shards = []
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        c = _recon(w)
+        c.upload_events(*[e[a:b] for e in ev])
+        shards.append(c)
+    for _ in range(3):
+        total = sum(c.backproject() for c in shards)
+        for c in shards:
+            c.apply_update(total)
+    img = shards[0].read_image().cpu().numpy()
+    for c in shards:
+        c.close()
+    r = _recon(w)
+    r.upload_events(*ev)
+    r.iterate(3)
+    whole = r.read_image().cpu().numpy()
+    r.close()
+    assert rel_err(img, whole) <= ORDER_TOL
+    assert torch.isfinite(torch.from_numpy(img)).all()
+
+
+def test_backproject_then_apply_is_one_iteration():
+    """One context: backproject + apply_update of its own A = iterate(1); host
+    and device buffers give the same A."""
+    w = make_workload("small_5mm")
+    ev = w.events()
+    a = _recon(w)
+    a.upload_events(*ev)
+    b = _recon(w)
+    b.upload_events(*ev)
+    for _ in range(3):
+        A_dev = a.backproject()
+        A_host = a.backproject(out=np.empty((w.ny, w.nz), np.float32))
+        assert rel_err(A_host, A_dev.cpu().numpy(), frac=0.0) <= ORDER_TOL
+        a.apply_update(A_host)
+        b.iterate(1)
+    assert rel_err(a.read_image().cpu().numpy(), b.read_image().cpu().numpy()) <= ORDER_TOL
+    assert a.stats()["iterations"] == 3
+    assert a.stats()["sum_s_rho"] == pytest.approx(b.stats()["n_used"], rel=2e-6)
+    a.close()
+    b.close()
+
+
+def test_empty_shard_and_argument_errors():
+    from paper_1502_07478_gb300 import TspError
+    from paper_1502_07478_gb300._lib import TSP_EINVAL, TSP_ESTATE
+    w = make_workload("small_5mm", n_events=1000)
+    r = _recon(w)
+    with pytest.raises(TspError) as ei:
+        r.backproject()
+    assert ei.value.code == TSP_ESTATE
+    empty = np.zeros(0, np.float32)
+    r.upload_events(empty, empty, empty)
+    A = r.backproject()
+    assert float(A.abs().max()) == 0.0
+    bad = np.ones((w.ny, w.nz), np.float32)
+    bad[3, 4] = -1.0
+    with pytest.raises(TspError) as ei:
+        r.apply_update(bad)
+    assert ei.value.code == TSP_EINVAL
+    bad[3, 4] = np.nan
+    with pytest.raises(TspError):
+        r.apply_update(bad)
+    # nothing was applied: the image is still rho = 1
+    assert float((r.read_image() - 1.0).abs().max()) == 0.0
+    r.close()
+
+
+def test_wait_times_out_then_completes():
+    """tsp_wait returns TSP_ETIMEOUT while queued work is still running (a
+    limit of 0 ms against ~50 queued iterations), and 0 once it has finished;
+    the context stays usable."""
+    w = make_workload("paper_1mm", n_events=300_000)
+    r = _recon(w)
+    r.upload_events(*w.events())
+    r.iterate(1)
+    assert r.wait(60_000)
+    r.iterate(50)
+    assert r.wait(0) is False
+    assert r.wait(600_000) is True
+    st = r.stats()
+    assert st["sum_s_rho"] == pytest.approx(st["n_used"], rel=1e-5)
+    r.close()
