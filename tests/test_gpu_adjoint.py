@@ -3,7 +3,8 @@ oracle, the finite-difference check, the autograd binding and the sigma fit.
 
 Bar (adjoint workload): ||dg_rho|| / ||g_rho|| <= 1e-4 and
 g_sigma within 1e-3 relative at sigma = (14, 55) mm; an Adam fit of sigma from
-(14, 55) recovers the true (10, 42) within 2%.
+(14, 55) lands within 0.5% of the FP64 oracle's maximum-likelihood sigma on
+the same data, and within 2% of the true (10, 42).
 """
 import numpy as np
 import pytest
@@ -136,41 +137,86 @@ def test_autograd_function(prob):
     r.set_sigma(w.sigma_z, w.sigma_dl)
 
 
-def test_adam_recovers_sigma():
-    """Fit (log sigma_z, log sigma_dl) by Adam on -L with rho held at the true
-    phantom (rasterised at pixel centres, scaled so that sum s rho = N).
+def _mle_module():
+    import importlib.util
+    import os
+    spec = importlib.util.spec_from_file_location(
+        "sigma_mle", os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                  "sigma_mle.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
 
-    The fit uses 5-sigma windows: with 3-sigma windows the truncated kernel
-    loses about 1% of its mass and the gradient at fixed windows is biased
-    towards smaller sigma (the fit then runs away).  What remains is the bias
-    of the model itself (Laplace approximation, acceptance ignored by the
-    kernel): about 2-3% on each sigma for these data."""
+
+def _adam_fit(w, ev, rho_np, steps=500):
+    """Adam on -L/N over (log sigma_z, log sigma_dl) from (14, 55) mm, lr 1e-2
+    decayed to 1e-4 over the steps; returns the fitted sigma and the context."""
     import torch
     from paper_1502_07478_gb300 import LogLik, Recon
-    w = make_workload("adjoint_2mm", cut=5.0)
-    ev = w.events()
     r = Recon.from_workload(w)
     r.upload_events(*ev)
-    s = r.compute_sensitivity().double().cpu().numpy()
-    truth = w.phantom().rasterize(w.ny, w.nz, w.R, w.L)
-    truth *= w.n_events / float((s * truth).sum())
-    rho = torch.tensor(truth, dtype=torch.float32, device="cuda")
+    rho = torch.tensor(rho_np, dtype=torch.float32, device="cuda")
     logsig = torch.tensor(np.log([14.0, 55.0]), dtype=torch.float64, requires_grad=True)
     opt = torch.optim.Adam([logsig], lr=1e-2)
-    # decay lr from 1e-2 to 1e-4 over the 500 steps so the iterate settles
-    sched = torch.optim.lr_scheduler.ExponentialLR(opt, gamma=0.01 ** (1 / 500))
-    for _ in range(500):
+    sched = torch.optim.lr_scheduler.ExponentialLR(opt, gamma=0.01 ** (1 / steps))
+    for _ in range(steps):
         opt.zero_grad()
         loss = -LogLik.apply(r, rho, torch.exp(logsig)) / w.n_events
         loss.backward()
         opt.step()
         sched.step()
-    sig = torch.exp(logsig).detach().numpy()
-    print("fitted sigma", sig)
-    assert abs(sig[0] / w.sigma_z - 1) < 0.03, sig
-    assert abs(sig[1] / w.sigma_dl - 1) < 0.03, sig
+    return torch.exp(logsig).detach().numpy(), r, rho
+
+
+def test_adam_sigma_full_adjoint_workload():
+    """The same fit on all 1e6 events of the adjoint workload, against the
+    oracle's maximiser on those events (tests/golden/sigma_mle.py 1000000).
+    There the model's own bias is resolved: the oracle's maximum lies at
+    -2.3% (sigma_z) and +1.9% (sigma_dl) from the simulated (10, 42) mm with a
+    statistical spread of 0.6% and 0.2%, so the fit is held to the oracle
+    (0.5%) and to the truth only within 2.5%."""
+    m = _mle_module()
+    w, ev, rho_np = m.fit_data(1_000_000)
+    gold = m.read_golden(1_000_000)
+    sig, r, _ = _adam_fit(w, ev, rho_np)
+    r.close()
+    print("fitted sigma", sig, "oracle maximiser", gold["sigma_z"], gold["sigma_dl"])
+    assert abs(sig[0] / gold["sigma_z"] - 1) < 0.005, sig
+    assert abs(sig[1] / gold["sigma_dl"] - 1) < 0.005, sig
+    assert abs(sig[0] / w.sigma_z - 1) < 0.025, sig
+    assert abs(sig[1] / w.sigma_dl - 1) < 0.025, sig
+
+
+def test_adam_recovers_sigma():
+    """Fit (log sigma_z, log sigma_dl) by Adam on -L with rho held at the true
+    phantom (rasterised at pixel centres, scaled so that sum s rho = N), on the
+    sigma-fit data of tests/golden/sigma_mle.py (the first 1e5 events of the
+    adjoint workload, windows of 5 sigma rebuilt at every sigma, from
+    (14, 55) mm).
+
+    The bar is the FP64 oracle's own maximiser of the same likelihood on the
+    same data (stored by tests/golden/sigma_mle.py, re-derived by
+    tests/test_oracle_sigma_mle.py): the GPU fit lies within 0.5% of it, which
+    separates the kernels' error from the model's.  On these 1e5 events that
+    maximiser is -1.6% / +1.0% from the simulated (10, 42) mm (the model's bias
+    plus a statistical spread of 1.9% / 0.6%), so the fit also recovers the
+    truth within 2% here; the full workload resolves the bias (next test).
+
+    5-sigma windows: with 3-sigma windows the truncated kernel loses about 1%
+    of its mass and the gradient at fixed windows is biased towards smaller
+    sigma (the fit then runs away)."""
+    m = _mle_module()
+    w, ev, rho_np = m.fit_data()
+    gold = m.read_golden()
+    sig, r, rho = _adam_fit(w, ev, rho_np)
+    print("fitted sigma", sig, "oracle maximiser", gold["sigma_z"], gold["sigma_dl"])
+    assert abs(sig[0] / gold["sigma_z"] - 1) < 0.005, sig
+    assert abs(sig[1] / gold["sigma_dl"] - 1) < 0.005, sig
+    assert abs(sig[0] / w.sigma_z - 1) < 0.02, sig
+    assert abs(sig[1] / w.sigma_dl - 1) < 0.02, sig
     # converged: the gradient at the fitted point is small
     r.set_sigma(float(sig[0]), float(sig[1]))
     r.set_image(rho)
     _, _, gs = r.loglik_grad(want_rho=False)
     assert np.all(np.abs(gs * sig) / w.n_events < 1e-3), gs
+    r.close()
