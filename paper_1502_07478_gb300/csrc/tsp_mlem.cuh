@@ -10,13 +10,15 @@
 // image row of the event's window (or one side of it):
 //   pass 1: walk the lane's chord of the ellipse outward from its centre,
 //           evaluate P (Eq. kernel) in the log2 domain (one rsqrt and one ex2
-//           per pixel), keep P in registers and accumulate D_j = sum P rho'
-//           (the denominator of Eq. iter); warp shuffles and a named barrier
+//           per pixel, two pixels per packed f32x2 instruction), keep P in the
+//           lane's tensor memory and accumulate D_j = sum P rho' (the
+//           denominator of Eq. iter); warp shuffles and a named barrier
 //           reduce D_j over the group;
 //   pass 2: add P / D_j into the shared accumulator (shared-memory atomics: two
 //           groups may touch the same pixel).
-// Neighbouring lanes hold neighbouring rows; with the sheared frame and a row
-// stride of 1 mod 32 words their accesses at each step fall in distinct banks.
+// A warp's lanes hold 32 distinct rows (paired around the window's middle);
+// with the sheared frame and a row stride of 1 mod 32 words their accesses at
+// each step fall in distinct banks.
 // At the end of the item the accumulator is flushed to the global
 // back-projection A with one atomic add per touched pixel; the finalize kernel
 // then forms rho <- rho * A.
@@ -24,8 +26,9 @@
 // Relative to the paper's GPU design (one warp per event over its bounding
 // box, rho read through the texture cache, Sec. 4.2): lanes own chords of the
 // ellipse instead of bounding-box pixels (no ellipse-test waste), P is cached
-// in registers between the two passes as in the paper, and the scatter goes to
-// shared memory first.
+// between the two passes as in the paper but in tensor memory rather than
+// registers (so that 1024-thread blocks fit), and the scatter goes to shared
+// memory first.
 #pragma once
 
 #include <type_traits>
@@ -168,7 +171,35 @@ __device__ __forceinline__ void make_row(const Geo& g, const EvSig& es, const fl
     const int sc = ((lo + hi) >> 1) - z0row;               // stored column of the centre
     const int smin = __reduce_min_sync(0xffffffffu, has ? sc : 0x7fffffff);
     const int smax = __reduce_max_sync(0xffffffffu, has ? sc : (int)0x80000000);
-    if (!has) return;
+    if (!has) {
+        // A lane without pixels still gets an in-bounds address, in its own
+        // (virtual) row at the warp's common column: the packed passes run it
+        // through their unpredicated pairs with P = 0, and its own row keeps
+        // its accesses in a bank of their own (one dummy address shared by the
+        // idle lanes would make the warp's atomics collide).  Rows and columns
+        // are clamped to the frame; on a whole-image frame the flat index is
+        // clamped into the padded image, as is the global rho' address.
+        const int vr = min(max(iy - f.oy, 0), f.rh - 1);
+        const int col = min(max(smin <= smax ? (smin + (smax - smin) / 2) : (f.rw >> 1), 0),
+                            f.rw - 1);
+        const long long lo_i = LMAX / 2;
+        const long long hi_i = (long long)g.ny * g.nz + kPadFloats - LMAX / 2 - 1;
+        long long sidx = (long long)vr * f.stride + col;
+        if constexpr (SMEM) {
+            r.base = (unsigned)__cvta_generic_to_shared(base) + 4u * (unsigned)sidx;
+        } else {
+            sidx = min(max(sidx, lo_i), hi_i);
+            r.base = (unsigned long long)(base + sidx);
+        }
+        if constexpr (GLD) {
+            const int iyv = min(max(f.oy + vr, 0), g.ny - 1);
+            const int zv = f.zbase + (int)rintf(__fmul_rn(f.shear, (float)(f.oy + vr - f.Y0)));
+            const long long gi = min(max((long long)iyv * g.nz + min(max(zv + col, 0), g.nz - 1),
+                                         lo_i), hi_i);
+            r.gbase = (unsigned long long)(gimg + gi);
+        }
+        return;
+    }
     // The common origin is used only when it lies within 2 columns of the
     // lane's own chord centre cc and keeps the lane's walk within LMAX steps;
     // otherwise the lane starts at cc (then kAlt needs exactly hi - lo + 1 <=
@@ -375,6 +406,23 @@ __device__ __forceinline__ void tm_ld4(unsigned a, float& x0, float& x1, float& 
                  : "memory");
 }
 
+__device__ __forceinline__ void tm_st8(unsigned a, float x0, float x1, float x2, float x3, float x4,
+                                       float x5, float x6, float x7)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(a),
+                 "f"(x0), "f"(x1), "f"(x2), "f"(x3), "f"(x4), "f"(x5), "f"(x6), "f"(x7)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tm_ld8(unsigned a, float (&x)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]), "=f"(x[4]), "=f"(x[5]),
+                   "=f"(x[6]), "=f"(x[7])
+                 : "r"(a)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tm_wait_st()
 {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -457,6 +505,305 @@ __device__ __forceinline__ void pass2_step(const RowK<SMEM>& r, int maxlen, unsi
     }
 }
 
+// ---------------------------------------------------------------------------
+// Pair-packed MLEM and log-likelihood passes.
+//
+// A lane walks its chord two pixels at a time.  The arithmetic of the two
+// pixels of a pair is done by packed f32x2 instructions (one issue for both);
+// the SFU operations and the memory accesses stay per pixel.  Pair k (1-based)
+// holds the pixels at column offsets d0(k), d1(k) from the lane's origin:
+//   kAlt: (+k, -(k-1));  kPos: (2k-2, 2k-1);  kNeg: (-(2k-1), -2k)
+// so every traversal covers its pixels in LMAX/2 pairs.  The first pixel of
+// pair k lies on the lane's chord iff k <= la, the second iff k <= lb.  The
+// pairs up to the smallest limit of the warp's active lanes (kfast) run
+// without any test; the others, up to the largest limit (kmax), test each
+// pixel.  A lane without pixels evaluates P = 0 exactly (its exponent is
+// -1000, which ex2.approx.ftz flushes to zero) at an in-bounds address of its
+// own row (make_row), and constrains neither kfast nor kmax.  Along a row, with d the column offset:
+//   Q = Q0 + d dQ,  A = A0 + d dA,  E = C0 - s^2 = e0 + d (e1 + d e2),
+//   P = Q^(-1/2) 2^(E + A^2/Q)       (Eq. kernel in the log2 domain).
+template <int TRAV>
+__host__ __device__ constexpr int pair_d0(int k)
+{
+    return TRAV == kAlt ? k : (TRAV == kPos ? 2 * k - 2 : -(2 * k - 1));
+}
+template <int TRAV>
+__host__ __device__ constexpr int pair_d1(int k)
+{
+    return TRAV == kAlt ? -(k - 1) : (TRAV == kPos ? 2 * k - 1 : -2 * k);
+}
+
+template <bool SMEM>
+struct RowP {
+    typename std::conditional<SMEM, unsigned, unsigned long long>::type base;
+    unsigned long long gbase;   // rho' in global memory (tiles that stage only A)
+    int la, lb;
+};
+
+// The row constants as pairs (the same value twice) for the packed operations,
+// and the step of the pair offsets.
+struct PairC {
+    float2 Q0, dQ, A0, dA, e0, e1, e2, inc;
+};
+
+// Packed row of a lane from its scalar row constants.  active: the lane has
+// pixels.
+template <int TRAV, int LMAX, bool SMEM, bool GLD>
+__device__ __forceinline__ void pair_row(const RowK<SMEM>& r, bool active, RowP<SMEM>& q, PairC& c)
+{
+    float Q0 = r.Q0, dQ = r.dQ, A0 = r.A0, dA = r.dA;
+    float e0 = fmaf(-r.su0, r.su0, r.C0), e1 = -2.0f * r.su0 * r.dsu, e2 = -(r.dsu * r.dsu);
+    if (active) {
+        q.base = r.base;
+        q.gbase = r.gbase;
+        if (TRAV == kAlt) {
+            q.la = r.lim_odd >> 1;
+            q.lb = (r.lim_even + 1) >> 1;
+        } else {
+            q.la = (r.lim_odd + 1) >> 1;
+            q.lb = r.lim_odd >> 1;
+        }
+    } else {
+        // no pixels: P = 0 at the lane's in-bounds idle address (make_row); no
+        // pixel is inside, so the predicated pairs skip the lane
+        q.base = r.base;
+        q.gbase = r.gbase;
+        q.la = q.lb = 0;
+        Q0 = 1.0f;
+        dQ = A0 = dA = e1 = e2 = 0.0f;
+        e0 = -1000.0f;
+    }
+    c.Q0 = make_float2(Q0, Q0);
+    c.dQ = make_float2(dQ, dQ);
+    c.A0 = make_float2(A0, A0);
+    c.dA = make_float2(dA, dA);
+    c.e0 = make_float2(e0, e0);
+    c.e1 = make_float2(e1, e1);
+    c.e2 = make_float2(e2, e2);
+    c.inc = make_float2((float)(pair_d0<TRAV>(2) - pair_d0<TRAV>(1)),
+                        (float)(pair_d1<TRAV>(2) - pair_d1<TRAV>(1)));
+}
+
+// Running addresses of a lane's two pixel streams: the first pixels of the
+// pairs (byte address a0 of pair k) and the second ones (a1); a pair step moves
+// them by the traversal's pixel step times 4 bytes.  The chunk loops below
+// advance them two pairs at a time, so every access uses a register address
+// plus a small immediate and the loops need no unrolled copies per chunk.
+template <int TRAV>
+__host__ __device__ constexpr int pair_step0() { return pair_d0<TRAV>(2) - pair_d0<TRAV>(1); }
+template <int TRAV>
+__host__ __device__ constexpr int pair_step1() { return pair_d1<TRAV>(2) - pair_d1<TRAV>(1); }
+
+// rho' at address A + OFF: unpredicated, or (PRED) only when k <= lim, else 0.
+template <bool SMEM, bool GLD, bool PRED, int OFF>
+__device__ __forceinline__ float ld_rhop(typename std::conditional<SMEM && !GLD, unsigned,
+                                                                   unsigned long long>::type a,
+                                         int k, int lim)
+{
+    float v;
+    if constexpr (GLD) {
+        if constexpr (PRED)
+            asm("{\n\t.reg .pred q;\n\tsetp.le.s32 q, %1, %2;\n\tmov.b32 %0, 0;\n\t"
+                "@q ld.global.nc.f32 %0, [%3+%4];\n\t}"
+                : "=&f"(v) : "r"(k), "r"(lim), "l"(a), "n"(OFF));
+        else
+            asm("ld.global.nc.f32 %0, [%1+%2];" : "=f"(v) : "l"(a), "n"(OFF));
+    } else if constexpr (SMEM) {
+        if constexpr (PRED)
+            asm volatile("{\n\t.reg .pred q;\n\tsetp.le.s32 q, %1, %2;\n\tmov.b32 %0, 0;\n\t"
+                         "@q ld.shared.f32 %0, [%3+%4];\n\t}"
+                         : "=&f"(v) : "r"(k), "r"(lim), "r"(a), "n"(OFF) : "memory");
+        else
+            asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF) : "memory");
+    } else {
+        if constexpr (PRED)
+            asm volatile("{\n\t.reg .pred q;\n\tsetp.le.s32 q, %1, %2;\n\tmov.b32 %0, 0;\n\t"
+                         "@q ld.global.f32 %0, [%3+%4];\n\t}"
+                         : "=&f"(v) : "r"(k), "r"(lim), "l"(a), "n"(OFF) : "memory");
+        else
+            asm volatile("ld.global.f32 %0, [%1+%2];" : "=f"(v) : "l"(a), "n"(OFF) : "memory");
+    }
+    return v;
+}
+
+// Pass 1 for one pair: kernel values of its two pixels (returned), the
+// denominator partial sums D2 += P rho'; kk holds the pair's offsets and is
+// advanced.  a0 / a1: addresses of the pair's two pixels (plus OFF0 / OFF1).
+template <bool SMEM, bool GLD, bool PRED, int OFF0, int OFF1, class Addr>
+__device__ __forceinline__ float2 p1_pair(Addr a0, Addr a1, int k, int la, int lb, const PairC& c,
+                                          float2& kk, float2& D2)
+{
+    const float2 q = __ffma2_rn(kk, c.dQ, c.Q0);
+    float2 rq;
+    rq.x = rsqrt_approx(q.x);
+    rq.y = rsqrt_approx(q.y);
+    const float2 a = __ffma2_rn(kk, c.dA, c.A0);
+    const float2 e = __ffma2_rn(kk, __ffma2_rn(kk, c.e2, c.e1), c.e0);
+    const float2 w = __fmul2_rn(a, rq);
+    const float2 g = __ffma2_rn(w, w, e);
+    float2 x;
+    x.x = ex2_approx(g.x);
+    x.y = ex2_approx(g.y);
+    const float2 p = __fmul2_rn(rq, x);
+    float2 v;
+    v.x = ld_rhop<SMEM, GLD, PRED, OFF0>(a0, k, la);
+    v.y = ld_rhop<SMEM, GLD, PRED, OFF1>(a1, k, lb);
+    D2 = __ffma2_rn(p, v, D2);
+    kk = __fadd2_rn(kk, c.inc);
+    return p;
+}
+
+// Pass 1 over pairs 1 .. kmax, two pairs (one tensor-memory store when ST) per
+// loop step: unpredicated while both pairs are <= kfast, then predicated.
+// Returns with D2 the two partial denominators.
+template <int TRAV, int LMAX, bool SMEM, bool GLD, bool ST>
+__device__ __forceinline__ void pass1_pairs(const RowP<SMEM>& r, const PairC& c, int kfast,
+                                            int kmax, float2& D2, unsigned tma)
+{
+    using Addr = typename std::conditional<SMEM && !GLD, unsigned, unsigned long long>::type;
+    constexpr int s0 = 4 * pair_step0<TRAV>(), s1 = 4 * pair_step1<TRAV>();
+    Addr a0, a1;
+    if constexpr (GLD) {
+        a0 = (Addr)(r.gbase + (unsigned long long)(4ll * pair_d0<TRAV>(1)));
+        a1 = (Addr)(r.gbase + (unsigned long long)(4ll * pair_d1<TRAV>(1)));
+    } else {
+        a0 = (Addr)(r.base + (Addr)(4ll * pair_d0<TRAV>(1)));
+        a1 = (Addr)(r.base + (Addr)(4ll * pair_d1<TRAV>(1)));
+    }
+    float2 kk = make_float2((float)pair_d0<TRAV>(1), (float)pair_d1<TRAV>(1));
+    unsigned col = tma;
+    int k = 1;
+    // four pairs per step (one 8-column store: fewer tensor-memory operations,
+    // each of which the warp must reach together), then two
+    for (; k + 3 <= kfast; k += 4) {
+        const float2 pa = p1_pair<SMEM, GLD, false, 0, 0>(a0, a1, k, r.la, r.lb, c, kk, D2);
+        const float2 pb = p1_pair<SMEM, GLD, false, s0, s1>(a0, a1, k + 1, r.la, r.lb, c, kk, D2);
+        const float2 pc = p1_pair<SMEM, GLD, false, 2 * s0, 2 * s1>(a0, a1, k + 2, r.la, r.lb, c,
+                                                                    kk, D2);
+        const float2 pd = p1_pair<SMEM, GLD, false, 3 * s0, 3 * s1>(a0, a1, k + 3, r.la, r.lb, c,
+                                                                    kk, D2);
+        if constexpr (ST) tm_st8(col, pa.x, pa.y, pb.x, pb.y, pc.x, pc.y, pd.x, pd.y);
+        a0 += (Addr)(4 * s0);
+        a1 += (Addr)(4 * s1);
+        col += 8;
+    }
+    for (; k + 1 <= kfast; k += 2) {
+        const float2 pa = p1_pair<SMEM, GLD, false, 0, 0>(a0, a1, k, r.la, r.lb, c, kk, D2);
+        const float2 pb = p1_pair<SMEM, GLD, false, s0, s1>(a0, a1, k + 1, r.la, r.lb, c, kk, D2);
+        if constexpr (ST) tm_st4(col, pa.x, pa.y, pb.x, pb.y);
+        a0 += (Addr)(2 * s0);
+        a1 += (Addr)(2 * s1);
+        col += 4;
+    }
+    for (; k <= kmax; k += 2) {
+        const float2 pa = p1_pair<SMEM, GLD, true, 0, 0>(a0, a1, k, r.la, r.lb, c, kk, D2);
+        const float2 pb = p1_pair<SMEM, GLD, true, s0, s1>(a0, a1, k + 1, r.la, r.lb, c, kk, D2);
+        if constexpr (ST) tm_st4(col, pa.x, pa.y, pb.x, pb.y);
+        a0 += (Addr)(2 * s0);
+        a1 += (Addr)(2 * s1);
+        col += 4;
+    }
+    (void)LMAX;
+}
+
+// acc += v at the four pixels of pairs k, k + 1 (addresses a0, a0 + S0 for the
+// first pixels, a1, a1 + S1 for the second ones), in one asm block.  PRED: each
+// pixel only when its pair lies inside (k <= la, k <= lb, k + 1 <= la,
+// k + 1 <= lb); else every pixel of a lane with pixels (act != 0) -- lanes
+// without pixels add nothing, which keeps them off the atomic unit.
+template <bool SMEM, bool PRED, int S0, int S1, class Addr>
+__device__ __forceinline__ void red4(Addr a0, Addr a1, int k, int la, int lb, int act, float a,
+                                     float b, float c, float d)
+{
+    if constexpr (SMEM) {
+        if constexpr (PRED)
+            asm volatile(
+                "{\n\t.reg .pred p0, p1, p2, p3;\n\t.reg .s32 k1;\n\tadd.s32 k1, %0, 1;\n\t"
+                "setp.le.s32 p0, %0, %1;\n\tsetp.le.s32 p1, %0, %2;\n\t"
+                "setp.le.s32 p2, k1, %1;\n\tsetp.le.s32 p3, k1, %2;\n\t"
+                "@p0 red.shared.add.f32 [%3], %7;\n\t@p1 red.shared.add.f32 [%4], %8;\n\t"
+                "@p2 red.shared.add.f32 [%3+%5], %9;\n\t@p3 red.shared.add.f32 [%4+%6], %10;\n\t}"
+                ::"r"(k), "r"(la), "r"(lb), "r"(a0), "r"(a1), "n"(S0), "n"(S1), "f"(a), "f"(b),
+                "f"(c), "f"(d) : "memory");
+        else
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.s32 p, %0, 0;\n\t"
+                "@p red.shared.add.f32 [%1], %5;\n\t@p red.shared.add.f32 [%2], %6;\n\t"
+                "@p red.shared.add.f32 [%1+%3], %7;\n\t@p red.shared.add.f32 [%2+%4], %8;\n\t}"
+                ::"r"(act), "r"(a0), "r"(a1), "n"(S0), "n"(S1), "f"(a), "f"(b), "f"(c), "f"(d)
+                : "memory");
+    } else {
+        if constexpr (PRED)
+            asm volatile(
+                "{\n\t.reg .pred p0, p1, p2, p3;\n\t.reg .s32 k1;\n\tadd.s32 k1, %0, 1;\n\t"
+                "setp.le.s32 p0, %0, %1;\n\tsetp.le.s32 p1, %0, %2;\n\t"
+                "setp.le.s32 p2, k1, %1;\n\tsetp.le.s32 p3, k1, %2;\n\t"
+                "@p0 red.global.add.f32 [%3], %7;\n\t@p1 red.global.add.f32 [%4], %8;\n\t"
+                "@p2 red.global.add.f32 [%3+%5], %9;\n\t@p3 red.global.add.f32 [%4+%6], %10;\n\t}"
+                ::"r"(k), "r"(la), "r"(lb), "l"(a0), "l"(a1), "n"(S0), "n"(S1), "f"(a), "f"(b),
+                "f"(c), "f"(d) : "memory");
+        else
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.s32 p, %0, 0;\n\t"
+                "@p red.global.add.f32 [%1], %5;\n\t@p red.global.add.f32 [%2], %6;\n\t"
+                "@p red.global.add.f32 [%1+%3], %7;\n\t@p red.global.add.f32 [%2+%4], %8;\n\t}"
+                ::"r"(act), "l"(a0), "l"(a1), "n"(S0), "n"(S1), "f"(a), "f"(b), "f"(c), "f"(d)
+                : "memory");
+    }
+}
+
+// Pass 2 over pairs 1 .. kmax: acc += P / D, P loaded back from tensor memory
+// four values at a time; unpredicated up to kfast (lanes with pixels), then
+// predicated per pixel.  r.base addresses the accumulator.
+template <int TRAV, bool SMEM>
+__device__ __forceinline__ void pass2_pairs(const RowP<SMEM>& r, int act, int kfast, int kmax,
+                                            unsigned tma, float2 invD)
+{
+    using Addr = typename std::conditional<SMEM, unsigned, unsigned long long>::type;
+    constexpr int s0 = 4 * pair_step0<TRAV>(), s1 = 4 * pair_step1<TRAV>();
+    Addr a0 = (Addr)(r.base + (Addr)(4ll * pair_d0<TRAV>(1)));
+    Addr a1 = (Addr)(r.base + (Addr)(4ll * pair_d1<TRAV>(1)));
+    unsigned col = tma;
+    int k = 1;
+    for (; k + 3 <= kfast; k += 4) {
+        float x[8];
+        tm_ld8(col, x);
+        tm_wait_ld();
+        const float2 pa = __fmul2_rn(make_float2(x[0], x[1]), invD);
+        const float2 pb = __fmul2_rn(make_float2(x[2], x[3]), invD);
+        const float2 pc = __fmul2_rn(make_float2(x[4], x[5]), invD);
+        const float2 pd = __fmul2_rn(make_float2(x[6], x[7]), invD);
+        red4<SMEM, false, s0, s1>(a0, a1, k, r.la, r.lb, act, pa.x, pa.y, pb.x, pb.y);
+        red4<SMEM, false, s0, s1>(a0 + (Addr)(2 * s0), a1 + (Addr)(2 * s1), k + 2, r.la, r.lb, act,
+                                  pc.x, pc.y, pd.x, pd.y);
+        a0 += (Addr)(4 * s0);
+        a1 += (Addr)(4 * s1);
+        col += 8;
+    }
+    for (; k + 1 <= kfast; k += 2) {
+        float x0, x1, x2, x3;
+        tm_ld4(col, x0, x1, x2, x3);
+        tm_wait_ld();
+        const float2 pa = __fmul2_rn(make_float2(x0, x1), invD);
+        const float2 pb = __fmul2_rn(make_float2(x2, x3), invD);
+        red4<SMEM, false, s0, s1>(a0, a1, k, r.la, r.lb, act, pa.x, pa.y, pb.x, pb.y);
+        a0 += (Addr)(2 * s0);
+        a1 += (Addr)(2 * s1);
+        col += 4;
+    }
+    for (; k <= kmax; k += 2) {
+        float x0, x1, x2, x3;
+        tm_ld4(col, x0, x1, x2, x3);
+        tm_wait_ld();
+        const float2 pa = __fmul2_rn(make_float2(x0, x1), invD);
+        const float2 pb = __fmul2_rn(make_float2(x2, x3), invD);
+        red4<SMEM, true, s0, s1>(a0, a1, k, r.la, r.lb, act, pa.x, pa.y, pb.x, pb.y);
+        a0 += (Addr)(2 * s0);
+        a1 += (Addr)(2 * s1);
+        col += 4;
+    }
+}
+
 // One event processed by a group of G warps; the lane holds row rows.x + rowi
 // with traversal TRAV.  part: 6*G floats of shared scratch for the group's
 // cross-warp reduction (double-buffered by parity).
@@ -473,26 +820,41 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
     const int2 rws = evs.rows[e];
     RowK<SMEM> r;
     RowG rg;
-    // The gradient pass pairs rows around the middle of the window (lane-row
-    // 2k -> mid - k, 2k + 1 -> mid + k + 1), so that each warp holds rows of
-    // similar chord length and idles less (5% faster on the 2 mm adjoint
-    // workload; the MLEM pass times the same either way and keeps rows in order).
-    int ri = rowi;
-    if constexpr (GRAD) {
-        const int mid = (rws.y - 1) >> 1, k = rowi >> 1;
-        ri = (rowi & 1) ? mid + k + 1 : mid - k;
-    }
+    // Rows are paired around the middle of the window (lane-row 2k -> mid - k,
+    // 2k + 1 -> mid + k + 1), so that each warp holds rows of similar chord
+    // length: its lanes run out of pixels at nearly the same step, which
+    // lengthens the unpredicated pairs of the packed passes and shortens the
+    // idle tail.  Rows 2k and 2k + 1 sit on opposite sides of the middle, an
+    // odd distance apart, so a warp's 32 rows still fall in 32 distinct banks
+    // at a common column.
+    const int mid = (rws.y - 1) >> 1, k = rowi >> 1;
+    const int ri = (rowi & 1) ? mid + k + 1 : mid - k;
     // KZ: the event's own sigma_z (z profile); else the context's constants
     make_row<TRAV, LMAX, GRAD, SMEM, GLD>(g, KZ ? ev_sig(g, ev) : geo_sig(g), ev, evs.geo64 + e,
                                           rws.x + ri, ri >= 0 && ri < rws.y, f,
                                           GLD ? acc_base : rp_base, rp_base, r, rg, bs);
-    const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(r.lim_odd, r.lim_even));
+    float D = 0.0f, Ez = 0.0f, El = 0.0f;
     float P[4];
-    float Dp = 0.0f, Ez = 0.0f, El = 0.0f;
-    pass1_step<TRAV, LMAX, GRAD, SMEM, GLD, MODE != kLoglik, 0>(r, rg, maxlen, tma, P, Dp, Ez,
-                                                                 El);
+    int maxlen = 0, kfast = 0, kmax = 0;
+    RowP<SMEM> q;
+    const bool active = max(r.lim_odd, r.lim_even) > 0;
+    if constexpr (!GRAD) {
+        PairC c;
+        pair_row<TRAV, LMAX, SMEM, GLD>(r, active, q, c);
+        kmax = __reduce_max_sync(0xffffffffu, active ? max(q.la, q.lb) : 0);
+        // (a warp without active lanes has kmax = 0 and does no pair at all)
+        kfast = min(kmax, __reduce_min_sync(0xffffffffu, active ? min(q.la, q.lb) : LMAX / 2));
+        float2 D2 = make_float2(0.0f, 0.0f);
+        pass1_pairs<TRAV, LMAX, SMEM, GLD, MODE != kLoglik>(q, c, kfast, kmax, D2, tma);
+        D = D2.x + D2.y;
+    } else {
+        maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(r.lim_odd, r.lim_even));
+        float Dp = 0.0f;
+        pass1_step<TRAV, LMAX, GRAD, SMEM, GLD, true, 0>(r, rg, maxlen, tma, P, Dp, Ez, El);
+        D = Dp;
+    }
     if (MODE != kLoglik) tm_wait_st();
-    float D = warp_sum(Dp);
+    D = warp_sum(D);
     if (GRAD) {
         Ez = warp_sum(Ez);
         El = warp_sum(El);
@@ -531,10 +893,17 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
         if (MODE != kLoglik) {
             // the accumulator has the rho' buffer's layout at a fixed byte offset
             // (GLD: the frame already addresses the accumulator)
-            RowK<SMEM> ra = r;
-            if (!GLD)
-                ra.base += (decltype(ra.base))((const char*)acc_base - (const char*)rp_base);
-            pass2_step<TRAV, LMAX, SMEM, 0>(ra, maxlen, tma, P, 1.0f / D);
+            const auto off = (decltype(r.base))((const char*)acc_base - (const char*)rp_base);
+            const float invD = 1.0f / D;
+            if constexpr (!GRAD) {
+                if (!GLD) q.base += off;
+                const float2 invD2 = make_float2(invD, invD);
+                pass2_pairs<TRAV, SMEM>(q, (int)active, kfast, kmax, tma, invD2);
+            } else {
+                RowK<SMEM> ra = r;
+                if (!GLD) ra.base += off;
+                pass2_step<TRAV, LMAX, SMEM, 0>(ra, maxlen, tma, P, invD);
+            }
         }
     }
 }
