@@ -520,6 +520,35 @@ def stress_record(workload, inputs, steps: int, warmup_iters: int, with_e2e: boo
     }
 
 
+def main_batched(args, ws):
+    """--workload batched_64: the batched-vs-plain comparison alone, as the
+    line (value = the batched form's event-iterations/s)."""
+    if ws > 1:
+        print(json.dumps({"error": "the batched workload runs on one GPU"}))
+        return 1
+    import torch
+    if not torch.cuda.is_available():
+        print(json.dumps({"error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    b = bench_batched(steps=args.steps, warmup=max(1, args.warmup))
+    clk = clocks.stop()
+    line = {"metric": METRIC, "value": b["batched"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": max(1, args.warmup),
+            "ms_per_step": b["ms_per_step"]["batched"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded phantom events, 64 reconstructions)",
+            "config": {"workload": "batched_64", "instances": b["instances"], "events": b["events"],
+                       "iterations_per_step": b["iterations_per_step"],
+                       "pixel_mm": b["pixel_mm"], "form": "batched (one Batch) vs 64 plain contexts",
+                       "parallelism": "1 GPU"},
+            "batched": b, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def bench_stress(args, workload):
     """--workload stress_05mm: the stress record as the bench line, with its
     end-to-end leg and the CPU baseline.  Warm-up is 3 single iterations."""
@@ -536,7 +565,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tsp", choices=["tsp", "reference"])
-    ap.add_argument("--workload", default="paper_1mm")
+    ap.add_argument("--workload", default="paper_1mm",
+                    help="paper_1mm (default), stress_05mm, batched_64, or another synth workload")
     ap.add_argument("--n-events", type=int, default=None, help="override the event count")
     ap.add_argument("--iters", type=int, default=None, help="override iterations per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -551,6 +581,14 @@ def main():
 
     from synth import make_workload
     ws, rank, local = _dist()
+    if args.workload == "batched_64":
+        if args.impl == "reference":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable":
+                                  "the batched comparison has no CPU reference arm; the oracle "
+                                  "is timed on the paper_1mm workload"}))
+            return 0
+        return main_batched(args, ws)
     over = {}
     if args.n_events:
         over["n_events"] = args.n_events

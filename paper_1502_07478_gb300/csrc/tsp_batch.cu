@@ -27,6 +27,7 @@ struct BatchClass {
     int lmax = 0, nseg = 1;
     bool kz = false;           // some member has a z-dependent sigma_z
     size_t smem = 0;
+    double work = 0.0;         // estimated pass work (events x window pixels)
     int4* items = nullptr;
     int4* oitems = nullptr;
     int n_items = 0, n_oitems = 0, items_cap = 0, oitems_cap = 0;
@@ -46,6 +47,15 @@ struct tsp_batch {
     int n_cls = 0;
     int* queue = nullptr;       // one work counter per class
     cudaStream_t cap_stream = nullptr;
+    // The classes' tile launches run as parallel branches (one stream each,
+    // forked from and joined back into the pass's stream), the class with
+    // the most work launched first: blocks of a later class take the SMs that
+    // an earlier class's blocks leave at the end of their queue, instead of
+    // each launch ending in its own tail.
+    cudaStream_t cls_stream[kMaxClasses] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kMaxClasses] = {};
+    int cls_order[kMaxClasses] = {};
     std::map<int, tsp_ctx::Graph> graphs;
     int last_graph = -1;
     bool profiling = false;
@@ -172,6 +182,7 @@ int rebuild(tsp_batch* b, cudaStream_t st)
         bc.nseg = cls_nseg[q];
         bc.kz = false;
         bc.smem = 0;
+        bc.work = 0.0;
         std::vector<std::vector<int4>> lists;
         std::vector<int> members;
         std::vector<int4> outl;
@@ -207,6 +218,7 @@ int rebuild(tsp_batch* b, cudaStream_t st)
                 const double stage = 0.25 * c->tl.RH * c->tl.RS;
                 for (const int4& it : lists[m]) cost.emplace_back(it.z * w + stage, it);
             }
+            for (const auto& x : cost) bc.work += x.first;
             std::stable_sort(cost.begin(), cost.end(),
                              [](const auto& x, const auto& y) { return x.first > y.first; });
             items.reserve(cost.size());
@@ -221,7 +233,12 @@ int rebuild(tsp_batch* b, cudaStream_t st)
                     }
                 if (!any) break;
             }
+            for (size_t m = 0; m < members.size(); ++m) {
+                const tsp_ctx* c = b->inst[members[m]];
+                for (const int4& it : lists[m]) bc.work += it.z * window_pixels(c);
+            }
         }
+        for (const int4& it : outl) bc.work += it.z * window_pixels(b->inst[it.w]);
         if (bc.smem > limit) return bfail(b, TSP_EINVAL, "tile region exceeds the shared memory");
         BATCH_CUDA(b, prepare_batch_pass(bc.lmax, limit));
         if ((int)items.size() > bc.items_cap) {
@@ -250,6 +267,9 @@ int rebuild(tsp_batch* b, cudaStream_t st)
                                   cudaMemcpyHostToDevice, st));
     BATCH_CUDA(b, cudaStreamSynchronize(st));
     b->n_cls = n_cls;
+    for (int q = 0; q < n_cls; ++q) b->cls_order[q] = q;
+    std::stable_sort(b->cls_order, b->cls_order + n_cls,
+                     [b](int x, int y) { return b->cls[x].work > b->cls[y].work; });
     b->max_npix = max_npix;
     clear_batch_graphs(b);
     b->dirty = false;
@@ -281,12 +301,22 @@ long long batch_pass_launches(const tsp_batch* b)
     return n;
 }
 
-// One batched pass (MODE kMlem or kGrad): the tile passes of every class.
+// One batched pass (MODE kMlem or kGrad): the tile passes of every class, as
+// parallel branches forked from and joined back into st (also inside a
+// stream capture), largest estimated work first.
 cudaError_t launch_batch_passes(const tsp_batch* b, int mode, cudaStream_t st)
 {
-    cudaError_t e = cudaSuccess;
-    for (int q = 0; q < b->n_cls && e == cudaSuccess; ++q)
-        e = launch_batch_pass(b->cls[q].lmax, mode, batch_args(b, q), st);
+    if (b->n_cls == 1) return launch_batch_pass(b->cls[0].lmax, mode, batch_args(b, 0), st);
+    cudaError_t e = cudaEventRecord(b->fork_ev, st);
+    for (int j = 0; j < b->n_cls && e == cudaSuccess; ++j) {
+        const int q = b->cls_order[j];
+        cudaStream_t cs = b->cls_stream[j];
+        e = cudaStreamWaitEvent(cs, b->fork_ev, 0);
+        if (e == cudaSuccess) e = launch_batch_pass(b->cls[q].lmax, mode, batch_args(b, q), cs);
+        if (e == cudaSuccess) e = cudaEventRecord(b->join_ev[j], cs);
+    }
+    for (int j = 0; j < b->n_cls && e == cudaSuccess; ++j)
+        e = cudaStreamWaitEvent(st, b->join_ev[j], 0);
     return e;
 }
 
@@ -439,6 +469,11 @@ int tsp_batch_create(const tsp_params* params, int k, tsp_batch** out)
     if (e == cudaSuccess) e = dmalloc(&b->queue, sizeof(int) * kMaxClasses);
     if (e == cudaSuccess) e = cudaMemset(b->queue, 0, sizeof(int) * kMaxClasses);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+    for (int q = 0; q < kMaxClasses && e == cudaSuccess; ++q) {
+        e = cudaStreamCreateWithFlags(&b->cls_stream[q], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev[q], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         b->err = std::string("tsp_batch_create: ") + cudaGetErrorString(e);
         return bail(e == cudaErrorMemoryAllocation ? TSP_ENOMEM : TSP_ECUDA);
@@ -454,6 +489,11 @@ void tsp_batch_destroy(tsp_batch* b)
     cudaDeviceSynchronize();
     clear_batch_graphs(b);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    for (int q = 0; q < kMaxClasses; ++q) {
+        if (b->cls_stream[q]) cudaStreamDestroy(b->cls_stream[q]);
+        if (b->join_ev[q]) cudaEventDestroy(b->join_ev[q]);
+    }
     dfree(b->table);
     dfree(b->imgs);
     for (BatchClass& bc : b->cls) {
