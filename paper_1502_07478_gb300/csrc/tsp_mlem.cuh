@@ -644,10 +644,20 @@ __device__ __forceinline__ float2 p1_pair(Addr a0, Addr a1, int k, int la, int l
     float2 x;
     x.x = ex2_approx(g.x);
     x.y = ex2_approx(g.y);
-    const float2 p = __fmul2_rn(rq, x);
+    float2 p = __fmul2_rn(rq, x);
+    if constexpr (PRED) {
+        // beyond the lane's chord P is 0 exactly: the denominator ignores the
+        // pixel and pass 2 may add the (zero) value without a predicate
+        p.x = k <= la ? p.x : 0.0f;
+        p.y = k <= lb ? p.y : 0.0f;
+    }
+    // A staged region has slack around it, so its loads need no predicate
+    // (the values of pixels outside the chord meet P = 0); loads from a global
+    // image keep theirs, as the chord's offsets may run past the image's start.
+    constexpr bool kLdPred = PRED && !(SMEM && !GLD);
     float2 v;
-    v.x = ld_rhop<SMEM, GLD, PRED, OFF0>(a0, k, la);
-    v.y = ld_rhop<SMEM, GLD, PRED, OFF1>(a1, k, lb);
+    v.x = ld_rhop<SMEM, GLD, kLdPred, OFF0>(a0, k, la);
+    v.y = ld_rhop<SMEM, GLD, kLdPred, OFF1>(a1, k, lb);
     D2 = __ffma2_rn(p, v, D2);
     kk = __fadd2_rn(kk, c.inc);
     return p;
@@ -707,31 +717,24 @@ __device__ __forceinline__ void pass1_pairs(const RowP<SMEM>& r, const PairC& c,
 }
 
 // acc += v at the four pixels of pairs k, k + 1 (addresses a0, a0 + S0 for the
-// first pixels, a1, a1 + S1 for the second ones), in one asm block.  PRED: each
-// pixel only when its pair lies inside (k <= la, k <= lb, k + 1 <= la,
-// k + 1 <= lb); else every pixel of a lane with pixels (act != 0) -- lanes
-// without pixels add nothing, which keeps them off the atomic unit.
+// first pixels, a1, a1 + S1 for the second ones), in one asm block.  In shared
+// memory unconditionally: outside a lane's chord its values are 0 (pass 1
+// zeroes P there) and its addresses stay inside the region's slack, and a lane
+// without pixels adds zeros in its own row; predicated atomics would cost a
+// branch and a reconvergence barrier each.  In global memory (the whole-image
+// frame, where the offsets may run past the image's start) with predicates:
+// PRED, each pixel only when its pair lies inside (k <= la, k <= lb,
+// k + 1 <= la, k + 1 <= lb); else every pixel of a lane with pixels (act).
 template <bool SMEM, bool PRED, int S0, int S1, class Addr>
 __device__ __forceinline__ void red4(Addr a0, Addr a1, int k, int la, int lb, int act, float a,
                                      float b, float c, float d)
 {
     if constexpr (SMEM) {
-        if constexpr (PRED)
-            asm volatile(
-                "{\n\t.reg .pred p0, p1, p2, p3;\n\t.reg .s32 k1;\n\tadd.s32 k1, %0, 1;\n\t"
-                "setp.le.s32 p0, %0, %1;\n\tsetp.le.s32 p1, %0, %2;\n\t"
-                "setp.le.s32 p2, k1, %1;\n\tsetp.le.s32 p3, k1, %2;\n\t"
-                "@p0 red.shared.add.f32 [%3], %7;\n\t@p1 red.shared.add.f32 [%4], %8;\n\t"
-                "@p2 red.shared.add.f32 [%3+%5], %9;\n\t@p3 red.shared.add.f32 [%4+%6], %10;\n\t}"
-                ::"r"(k), "r"(la), "r"(lb), "r"(a0), "r"(a1), "n"(S0), "n"(S1), "f"(a), "f"(b),
-                "f"(c), "f"(d) : "memory");
-        else
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.s32 p, %0, 0;\n\t"
-                "@p red.shared.add.f32 [%1], %5;\n\t@p red.shared.add.f32 [%2], %6;\n\t"
-                "@p red.shared.add.f32 [%1+%3], %7;\n\t@p red.shared.add.f32 [%2+%4], %8;\n\t}"
-                ::"r"(act), "r"(a0), "r"(a1), "n"(S0), "n"(S1), "f"(a), "f"(b), "f"(c), "f"(d)
-                : "memory");
+        (void)k, (void)la, (void)lb, (void)act;
+        asm volatile(
+            "red.shared.add.f32 [%0], %4;\n\tred.shared.add.f32 [%1], %5;\n\t"
+            "red.shared.add.f32 [%0+%2], %6;\n\tred.shared.add.f32 [%1+%3], %7;"
+            ::"r"(a0), "r"(a1), "n"(S0), "n"(S1), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
     } else {
         if constexpr (PRED)
             asm volatile(
@@ -753,8 +756,9 @@ __device__ __forceinline__ void red4(Addr a0, Addr a1, int k, int la, int lb, in
 }
 
 // Pass 2 over pairs 1 .. kmax: acc += P / D, P loaded back from tensor memory
-// four values at a time; unpredicated up to kfast (lanes with pixels), then
-// predicated per pixel.  r.base addresses the accumulator.
+// eight or four values at a time (P is 0 outside each lane's chord); the
+// shared-memory forms add every pixel, the global ones only the chord's.
+// r.base addresses the accumulator.
 template <int TRAV, bool SMEM>
 __device__ __forceinline__ void pass2_pairs(const RowP<SMEM>& r, int act, int kfast, int kmax,
                                             unsigned tma, float2 invD)
