@@ -162,8 +162,11 @@ int tsp_iterate(tsp_ctx* ctx, int n_iter, void* stream);
  * current image,
  *   A_out[l] = sum_j P(e_j|l) / D_j,   D_j = sum_i P(e_j|i) s_i rho_i,
  * over the events with D_j > 0 (ny*nz floats, host or device per on_device),
- * with the kernel P of Eq. kernel (Sec. 3) over each event's window.  The
- * image is not changed; tsp_stats then reports the events used.  Requires an
+ * with the kernel P of Eq. kernel (Sec. 3) over each event's window.  At a
+ * pixel with s_l rho_l = 0 (which the update keeps at 0 whatever A is) A_out[l]
+ * holds only the terms of events on the global-memory path: the tile pass
+ * sums the terms P s_l rho_l / D_j and divides by s_l rho_l, so it adds
+ * nothing there.  The image is not changed; tsp_stats then reports the events used.  Requires an
  * upload (TSP_ESTATE; an empty list gives A = 0).  A host A_out is filled when
  * the call returns; a device A_out is written asynchronously on stream.
  *

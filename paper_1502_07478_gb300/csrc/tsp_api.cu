@@ -121,12 +121,16 @@ int plan(tsp_ctx* c)
     tl.RS = RS;
     tl.RW = RS;
     tl.TZ = RS - 2 * tl.HZ;
-    const size_t budget = 200 * 1024;
+    const size_t budget = 216 * 1024;
+    auto fits = [&](int ty) {
+        return tiles_region_fits(ty + 2 * tl.HY, RS) &&
+               tiles_smem_floats(ty + 2 * tl.HY, RS) * sizeof(float) <= budget;
+    };
     int TY = std::max(4, std::min(128, c->sched.ty_cap) / 4 * 4);
     const int ty0 = TY;
-    while (TY > 4 && tiles_smem_floats(TY + 2 * tl.HY, RS) * sizeof(float) > budget) TY -= 4;
+    while (TY > 4 && !fits(TY)) TY -= 4;
     c->gld = 0;
-    if (tiles_smem_floats(TY + 2 * tl.HY, RS) * sizeof(float) > budget) {
+    if (!fits(TY)) {
         // windows too large to stage rho' and the accumulator (very fine
         // grids): stage only the accumulator and read rho' from global memory,
         // with two lanes per row; if even that does not fit, no angle bins, so
@@ -325,7 +329,7 @@ int prepare_events(tsp_ctx* c, cudaStream_t st)
 long long item_events(long long placed, int items_per_sm, int sms)
 {
     const long long E = placed / ((long long)std::max(1, items_per_sm) * std::max(1, sms));
-    return std::max(32ll, std::min(4096ll, E));
+    return std::max(32ll, std::min((long long)kItemMaxEvents, E));
 }
 
 std::vector<int4> tile_items(const tsp_ctx* c, long long E, int w)

@@ -154,14 +154,47 @@ __device__ __forceinline__ int row_shift(const Tiling& tl, float shear, int iy)
     return (int)rintf(__fmul_rn(shear, (float)(iy - tl.Y0)));
 }
 
-// Shared-memory layout of the tile kernel, in floats: kPadFloats slack, the
-// rho' region (RH*RS), 2*kPadFloats slack, the accumulator region (RH*RS),
-// kPadFloats slack, then the groups' reduction slots (warps/G groups x 2
-// parities x 3G floats <= 6*kMaxWarps).
+// The MLEM tile pass accumulates, per pixel and work item, the responsibility
+// sum X = sum_j P_jl rho'_l / D_j (each term in [0, 1], since D_j >= P_jl rho'_l)
+// in fixed point over two 32-bit words, with native integer shared-memory adds
+// (a float add to shared memory is a compare-and-swap loop on this GPU).  Term
+// x is split as x 2^12 = H + L 2^-20 with H = floor(x 2^12) <= 4096 and
+// L = round((x 2^12 - H) 2^20) <= 2^20, both formed by adding the magic 2^23
+// in float and taking the bits (bits = 0x4B000000 + integer); the words are
+// added unreduced.  With at most kItemMaxEvents events an item (each event
+// adds a nonzero term to a pixel at most once), the H word's low 24 bits hold
+// sum H exactly (<= 4000 * 4097 < 2^24) and its top byte the magic's total,
+// which the L word received the same number of times:
+//   sum H = wh & 0xFFFFFF,   sum L = wl - (wh & 0xFF000000)   (mod 2^32, exact
+// as sum L <= 4000 * 2^20 < 2^32), X = (sum H + sum L 2^-20) 2^-12, quantum
+// 2^-32 per term.  The flush adds X / rho'_l to A.  (At a pixel with rho' = 0
+// the terms are 0 and the item adds nothing to A there; the update rho A is 0
+// at such a pixel either way.)
+constexpr int kItemMaxEvents = 4000;
+constexpr float kFxMagic = 8388608.0f;            // 2^23
+constexpr unsigned kFxMagicBits = 0x4B000000u;
+
+// Distance, in 32-bit words, from a pixel's H word to its L word: a
+// compile-time constant, so that the scatter reaches both words from one
+// register address.  A region of RH*RS <= kAccWords - 2*kPadFloats words
+// keeps the L region and both regions' slack apart.
+constexpr int kAccWords = 18432;
+
+// Shared-memory layout of the tile kernel, in 32-bit words: kPadFloats slack,
+// the rho' region (RH*RS), 2*kPadFloats slack, the accumulator's H region
+// (RH*RS; the float accumulator of the other passes), its L region at
+// kAccWords words from the H region, kPadFloats slack, then the groups'
+// reduction slots (warps/G groups x 2 parities x 3G floats <= 6*kMaxWarps).
 __host__ __device__ constexpr size_t tiles_smem_floats(int RH, int RS)
 {
-    return (size_t)kPadFloats + (size_t)RH * RS + 2 * kPadFloats + (size_t)RH * RS + kPadFloats +
-           6 * kMaxWarps;
+    return (size_t)kPadFloats + (size_t)RH * RS + 2 * kPadFloats + (size_t)kAccWords +
+           (size_t)RH * RS + kPadFloats + 6 * kMaxWarps;
+}
+
+// A staged region fits the two-word accumulator layout.
+__host__ __device__ constexpr bool tiles_region_fits(int RH, int RS)
+{
+    return (long long)RH * RS <= (long long)kAccWords - 2 * kPadFloats;
 }
 
 // The same with only the accumulator staged (rho' read from global memory).

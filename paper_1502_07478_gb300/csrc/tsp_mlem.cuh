@@ -626,10 +626,11 @@ __device__ __forceinline__ float ld_rhop(typename std::conditional<SMEM && !GLD,
     return v;
 }
 
-// Pass 1 for one pair: kernel values of its two pixels (returned), the
-// denominator partial sums D2 += P rho'; kk holds the pair's offsets and is
-// advanced.  a0 / a1: addresses of the pair's two pixels (plus OFF0 / OFF1).
-template <bool SMEM, bool GLD, bool PRED, int OFF0, int OFF1, class Addr>
+// Pass 1 for one pair: kernel values of its two pixels, or (PV) their
+// products P rho' (returned), the denominator partial sums D2 += P rho'; kk
+// holds the pair's offsets and is advanced.  a0 / a1: addresses of the pair's
+// two pixels (plus OFF0 / OFF1).
+template <bool SMEM, bool GLD, bool PRED, bool PV, int OFF0, int OFF1, class Addr>
 __device__ __forceinline__ float2 p1_pair(Addr a0, Addr a1, int k, int la, int lb, const PairC& c,
                                           float2& kk, float2& D2)
 {
@@ -658,15 +659,21 @@ __device__ __forceinline__ float2 p1_pair(Addr a0, Addr a1, int k, int la, int l
     float2 v;
     v.x = ld_rhop<SMEM, GLD, kLdPred, OFF0>(a0, k, la);
     v.y = ld_rhop<SMEM, GLD, kLdPred, OFF1>(a1, k, lb);
-    D2 = __ffma2_rn(p, v, D2);
     kk = __fadd2_rn(kk, c.inc);
-    return p;
+    if constexpr (PV) {
+        const float2 pv = __fmul2_rn(p, v);
+        D2 = __fadd2_rn(D2, pv);
+        return pv;
+    } else {
+        D2 = __ffma2_rn(p, v, D2);
+        return p;
+    }
 }
 
 // Pass 1 over pairs 1 .. kmax, two pairs (one tensor-memory store when ST) per
 // loop step: unpredicated while both pairs are <= kfast, then predicated.
-// Returns with D2 the two partial denominators.
-template <int TRAV, int LMAX, bool SMEM, bool GLD, bool ST>
+// Returns with D2 the two partial denominators; PV stores P rho' instead of P.
+template <int TRAV, int LMAX, bool SMEM, bool GLD, bool ST, bool PV>
 __device__ __forceinline__ void pass1_pairs(const RowP<SMEM>& r, const PairC& c, int kfast,
                                             int kmax, float2& D2, unsigned tma)
 {
@@ -686,28 +693,31 @@ __device__ __forceinline__ void pass1_pairs(const RowP<SMEM>& r, const PairC& c,
     // four pairs per step (one 8-column store: fewer tensor-memory operations,
     // each of which the warp must reach together), then two
     for (; k + 3 <= kfast; k += 4) {
-        const float2 pa = p1_pair<SMEM, GLD, false, 0, 0>(a0, a1, k, r.la, r.lb, c, kk, D2);
-        const float2 pb = p1_pair<SMEM, GLD, false, s0, s1>(a0, a1, k + 1, r.la, r.lb, c, kk, D2);
-        const float2 pc = p1_pair<SMEM, GLD, false, 2 * s0, 2 * s1>(a0, a1, k + 2, r.la, r.lb, c,
-                                                                    kk, D2);
-        const float2 pd = p1_pair<SMEM, GLD, false, 3 * s0, 3 * s1>(a0, a1, k + 3, r.la, r.lb, c,
-                                                                    kk, D2);
+        const float2 pa = p1_pair<SMEM, GLD, false, PV, 0, 0>(a0, a1, k, r.la, r.lb, c, kk, D2);
+        const float2 pb = p1_pair<SMEM, GLD, false, PV, s0, s1>(a0, a1, k + 1, r.la, r.lb, c, kk,
+                                                                D2);
+        const float2 pc = p1_pair<SMEM, GLD, false, PV, 2 * s0, 2 * s1>(a0, a1, k + 2, r.la, r.lb,
+                                                                        c, kk, D2);
+        const float2 pd = p1_pair<SMEM, GLD, false, PV, 3 * s0, 3 * s1>(a0, a1, k + 3, r.la, r.lb,
+                                                                        c, kk, D2);
         if constexpr (ST) tm_st8(col, pa.x, pa.y, pb.x, pb.y, pc.x, pc.y, pd.x, pd.y);
         a0 += (Addr)(4 * s0);
         a1 += (Addr)(4 * s1);
         col += 8;
     }
     for (; k + 1 <= kfast; k += 2) {
-        const float2 pa = p1_pair<SMEM, GLD, false, 0, 0>(a0, a1, k, r.la, r.lb, c, kk, D2);
-        const float2 pb = p1_pair<SMEM, GLD, false, s0, s1>(a0, a1, k + 1, r.la, r.lb, c, kk, D2);
+        const float2 pa = p1_pair<SMEM, GLD, false, PV, 0, 0>(a0, a1, k, r.la, r.lb, c, kk, D2);
+        const float2 pb = p1_pair<SMEM, GLD, false, PV, s0, s1>(a0, a1, k + 1, r.la, r.lb, c, kk,
+                                                                D2);
         if constexpr (ST) tm_st4(col, pa.x, pa.y, pb.x, pb.y);
         a0 += (Addr)(2 * s0);
         a1 += (Addr)(2 * s1);
         col += 4;
     }
     for (; k <= kmax; k += 2) {
-        const float2 pa = p1_pair<SMEM, GLD, true, 0, 0>(a0, a1, k, r.la, r.lb, c, kk, D2);
-        const float2 pb = p1_pair<SMEM, GLD, true, s0, s1>(a0, a1, k + 1, r.la, r.lb, c, kk, D2);
+        const float2 pa = p1_pair<SMEM, GLD, true, PV, 0, 0>(a0, a1, k, r.la, r.lb, c, kk, D2);
+        const float2 pb = p1_pair<SMEM, GLD, true, PV, s0, s1>(a0, a1, k + 1, r.la, r.lb, c, kk,
+                                                               D2);
         if constexpr (ST) tm_st4(col, pa.x, pa.y, pb.x, pb.y);
         a0 += (Addr)(2 * s0);
         a1 += (Addr)(2 * s1);
@@ -808,6 +818,70 @@ __device__ __forceinline__ void pass2_pairs(const RowP<SMEM>& r, int act, int kf
     }
 }
 
+// The fixed-point terms of two pairs (four pixels; pa = pair k, pb = pair k + 1,
+// .x the first pixels, .y the second ones) added into the H words at a0, a1,
+// a0 + S0, a1 + S1 and the L words kAccWords words further on.  v holds
+// P rho' and s2 = 2^12 / D, so x 2^12 = v s2:
+//   t1 = 2^23 + v s2 rounded toward zero   (bits: magic + H, H = floor(x 2^12)),
+//   r  = v s2 - H                          (exact in the FMA, in [0, 1]),
+//   t2 = 2^23 + r 2^20 rounded to nearest  (bits: magic + L).
+template <int S0, int S1>
+__device__ __forceinline__ void fx4(unsigned a0, unsigned a1, float2 pa, float2 pb, float2 s2)
+{
+    const float2 M = make_float2(kFxMagic, kFxMagic);
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 sl = make_float2(1048576.0f, 1048576.0f);          // 2^20
+    const float2 ha = __ffma2_rz(pa, s2, M), hb = __ffma2_rz(pb, s2, M);
+    const float2 ra = __ffma2_rn(pa, s2, __ffma2_rn(ha, m1, M));    // v s2 - H
+    const float2 rb = __ffma2_rn(pb, s2, __ffma2_rn(hb, m1, M));
+    const float2 la = __ffma2_rn(ra, sl, M), lb = __ffma2_rn(rb, sl, M);
+    asm volatile(
+        "red.shared.add.u32 [%0], %4;\n\tred.shared.add.u32 [%1], %5;\n\t"
+        "red.shared.add.u32 [%0+%2], %6;\n\tred.shared.add.u32 [%1+%3], %7;\n\t"
+        "red.shared.add.u32 [%0+%12], %8;\n\tred.shared.add.u32 [%1+%12], %9;\n\t"
+        "red.shared.add.u32 [%0+%13], %10;\n\tred.shared.add.u32 [%1+%14], %11;"
+        ::"r"(a0), "r"(a1), "n"(S0), "n"(S1),
+        "r"(__float_as_uint(ha.x)), "r"(__float_as_uint(ha.y)), "r"(__float_as_uint(hb.x)),
+        "r"(__float_as_uint(hb.y)), "r"(__float_as_uint(la.x)), "r"(__float_as_uint(la.y)),
+        "r"(__float_as_uint(lb.x)), "r"(__float_as_uint(lb.y)), "n"(4 * kAccWords),
+        "n"(4 * kAccWords + S0), "n"(4 * kAccWords + S1)
+        : "memory");
+}
+
+// Pass 2 of the MLEM tile pass in fixed point: the terms x = P rho' / D of
+// pairs 1 .. kmax (P rho' loaded back from tensor memory, 0 outside each
+// lane's chord) added to the item's two-word accumulator at r.base (H words).
+template <int TRAV>
+__device__ __forceinline__ void pass2_fx(const RowP<true>& r, int kfast, int kmax, unsigned tma,
+                                         float2 s2)
+{
+    constexpr int s0 = 4 * pair_step0<TRAV>(), s1 = 4 * pair_step1<TRAV>();
+    unsigned a0 = r.base + (unsigned)(4 * pair_d0<TRAV>(1));
+    unsigned a1 = r.base + (unsigned)(4 * pair_d1<TRAV>(1));
+    unsigned col = tma;
+    int k = 1;
+    for (; k + 3 <= kfast; k += 4) {
+        float x[8];
+        tm_ld8(col, x);
+        tm_wait_ld();
+        fx4<s0, s1>(a0, a1, make_float2(x[0], x[1]), make_float2(x[2], x[3]), s2);
+        fx4<s0, s1>(a0 + (unsigned)(2 * s0), a1 + (unsigned)(2 * s1), make_float2(x[4], x[5]),
+                    make_float2(x[6], x[7]), s2);
+        a0 += (unsigned)(4 * s0);
+        a1 += (unsigned)(4 * s1);
+        col += 8;
+    }
+    for (; k <= kmax; k += 2) {
+        float x0, x1, x2, x3;
+        tm_ld4(col, x0, x1, x2, x3);
+        tm_wait_ld();
+        fx4<s0, s1>(a0, a1, make_float2(x0, x1), make_float2(x2, x3), s2);
+        a0 += (unsigned)(2 * s0);
+        a1 += (unsigned)(2 * s1);
+        col += 4;
+    }
+}
+
 // One event processed by a group of G warps; the lane holds row rows.x + rowi
 // with traversal TRAV.  part: 6*G floats of shared scratch for the group's
 // cross-warp reduction (double-buffered by parity).
@@ -820,6 +894,8 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
                                            int& parity, BlockSums* bs, unsigned tma)
 {
     constexpr bool GRAD = (MODE == kGrad);
+    // the MLEM pass over a staged region accumulates in fixed point (fx4)
+    constexpr bool kFx = (MODE == kMlem) && SMEM && !GLD;
     const float4 ev = evs.geo[e];
     const int2 rws = evs.rows[e];
     RowK<SMEM> r;
@@ -849,7 +925,7 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
         // (a warp without active lanes has kmax = 0 and does no pair at all)
         kfast = min(kmax, __reduce_min_sync(0xffffffffu, active ? min(q.la, q.lb) : LMAX / 2));
         float2 D2 = make_float2(0.0f, 0.0f);
-        pass1_pairs<TRAV, LMAX, SMEM, GLD, MODE != kLoglik>(q, c, kfast, kmax, D2, tma);
+        pass1_pairs<TRAV, LMAX, SMEM, GLD, MODE != kLoglik, kFx>(q, c, kfast, kmax, D2, tma);
         D = D2.x + D2.y;
     } else {
         maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(r.lim_odd, r.lim_even));
@@ -899,7 +975,11 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
             // (GLD: the frame already addresses the accumulator)
             const auto off = (decltype(r.base))((const char*)acc_base - (const char*)rp_base);
             const float invD = 1.0f / D;
-            if constexpr (!GRAD) {
+            if constexpr (kFx) {
+                q.base += off;
+                const float s = invD * 4096.0f;
+                pass2_fx<TRAV>(q, kfast, kmax, tma, make_float2(s, s));
+            } else if constexpr (!GRAD) {
                 if (!GLD) q.base += off;
                 const float2 invD2 = make_float2(invD, invD);
                 pass2_pairs<TRAV, SMEM>(q, (int)active, kfast, kmax, tma, invD2);
@@ -1017,6 +1097,8 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
     constexpr int kCols = tm_block_cols(LMAX, kWarps);
     if (warp == 0) tm_alloc<kCols>(&s_tmem);
     init_block_sums(&s_sums);
+    // the slack around the rho' region is read (times P = 0) by the
+    // unpredicated pass-1 loads, so it must hold finite values
     if (!BATCH) {
         const int region = p.tl.RH * p.tl.RS;
         float* s_rp = smem + kPadFloats;
@@ -1067,7 +1149,9 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
         const int region = tl.RH * tl.RS;
         float* s_rp = smem + kPadFloats;
         float* s_acc = GLD ? s_rp : s_rp + region + 2 * kPadFloats;
-        float* part = s_acc + region + kPadFloats + grp * (2 * 3 * G);
+        // the L words of the fixed-point accumulator (MLEM over a staged region)
+        unsigned* s_accL = reinterpret_cast<unsigned*>(s_acc) + kAccWords;
+        float* part = (GLD ? s_acc : s_acc + kAccWords) + region + kPadFloats + grp * (2 * 3 * G);
         int parity = 0;
         const Frame f = tile_frame(g, tl, item.x);
         if (tid == 0) s_frame = f;
@@ -1086,6 +1170,7 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
                         v = I.rhop[(size_t)iy * g.nz + iz];
                     s_rp[rr * tl.RS + cc] = v;
                     if (MODE != kLoglik) s_acc[rr * tl.RS + cc] = 0.0f;
+                    if (MODE == kMlem) s_accL[rr * tl.RS + cc] = 0u;
                 }
             }
         }
@@ -1103,7 +1188,18 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
                 const int z0row = f.zbase + (int)rintf(__fmul_rn(f.shear, (float)(iy - f.Y0)));
                 for (int cc = lane; cc < tl.RW; cc += 32) {
                     const int iz = z0row + cc;
-                    const float v = s_acc[rr * tl.RS + cc];
+                    const int k = rr * tl.RS + cc;
+                    float v;
+                    if (MODE == kMlem && !GLD) {
+                        // A += X / rho' (the fixed-point sums, see kAccWords)
+                        const unsigned wh = __float_as_uint(s_acc[k]), wl = s_accL[k];
+                        const unsigned sh = wh & 0xFFFFFFu, sl = wl - (wh & 0xFF000000u);
+                        const float X = fmaf((float)sl, 0x1p-32f, (float)sh * 0x1p-12f);
+                        const float rp = s_rp[k];
+                        v = rp > 0.0f ? X / rp : 0.0f;
+                    } else {
+                        v = s_acc[k];
+                    }
                     if (iz >= 0 && iz < g.nz && v != 0.0f)
                         atomicAdd(I.A + (size_t)iy * g.nz + iz, v);
                 }

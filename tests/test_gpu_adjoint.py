@@ -131,7 +131,7 @@ def test_autograd_function(prob):
     L.backward()
     r.set_image(rho.astype(np.float32))
     L2, g, gs = r.loglik_grad()
-    assert float(L) == pytest.approx(L2, rel=1e-9)
+    assert float(L.detach()) == pytest.approx(L2, rel=1e-9)
     torch.testing.assert_close(rho_t.grad, g, rtol=1e-6, atol=1e-6 * float(g.abs().max()))
     np.testing.assert_allclose(sig.grad.numpy(), gs, rtol=1e-9)
     r.set_sigma(w.sigma_z, w.sigma_dl)
