@@ -160,8 +160,8 @@ __device__ __forceinline__ int row_shift(const Tiling& tl, float shear, int iy)
 // (a float add to shared memory is a compare-and-swap loop on this GPU).  Term
 // x is split as x 2^12 = H + L 2^-20 with H = floor(x 2^12) <= 4096 and
 // L = round((x 2^12 - H) 2^20) <= 2^20, both formed by adding the magic 2^23
-// in float and taking the bits (bits = 0x4B000000 + integer); the words are
-// added unreduced.  With at most kItemMaxEvents events an item (each event
+// in float and taking the bits (bits = 0x4B000000 + integer; L from the
+// exact product inside an FMA); the words are added unreduced.  With at most kItemMaxEvents events an item (each event
 // adds a nonzero term to a pixel at most once), the H word's low 24 bits hold
 // sum H exactly (<= 4000 * 4097 < 2^24) and its top byte the magic's total,
 // which the L word received the same number of times:

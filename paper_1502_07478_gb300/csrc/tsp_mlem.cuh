@@ -423,6 +423,27 @@ __device__ __forceinline__ void tm_ld8(unsigned a, float (&x)[8])
                  : "memory");
 }
 
+__device__ __forceinline__ void tm_st16(unsigned a, const float (&x)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, "
+                 "%9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(a),
+                 "f"(x[0]), "f"(x[1]), "f"(x[2]), "f"(x[3]), "f"(x[4]), "f"(x[5]), "f"(x[6]),
+                 "f"(x[7]), "f"(x[8]), "f"(x[9]), "f"(x[10]), "f"(x[11]), "f"(x[12]), "f"(x[13]),
+                 "f"(x[14]), "f"(x[15])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tm_ld16(unsigned a, float (&x)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+                 "%10, %11, %12, %13, %14, %15}, [%16];"
+                 : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3]), "=f"(x[4]), "=f"(x[5]),
+                   "=f"(x[6]), "=f"(x[7]), "=f"(x[8]), "=f"(x[9]), "=f"(x[10]), "=f"(x[11]),
+                   "=f"(x[12]), "=f"(x[13]), "=f"(x[14]), "=f"(x[15])
+                 : "r"(a)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tm_wait_st()
 {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -670,8 +691,9 @@ __device__ __forceinline__ float2 p1_pair(Addr a0, Addr a1, int k, int la, int l
     }
 }
 
-// Pass 1 over pairs 1 .. kmax, two pairs (one tensor-memory store when ST) per
-// loop step: unpredicated while both pairs are <= kfast, then predicated.
+// Pass 1 over pairs 1 .. kmax, eight, four or two pairs (one tensor-memory
+// store when ST) per loop step: unpredicated while the pairs are <= kfast, then
+// two at a time predicated.
 // Returns with D2 the two partial denominators; PV stores P rho' instead of P.
 template <int TRAV, int LMAX, bool SMEM, bool GLD, bool ST, bool PV>
 __device__ __forceinline__ void pass1_pairs(const RowP<SMEM>& r, const PairC& c, int kfast,
@@ -690,8 +712,34 @@ __device__ __forceinline__ void pass1_pairs(const RowP<SMEM>& r, const PairC& c,
     float2 kk = make_float2((float)pair_d0<TRAV>(1), (float)pair_d1<TRAV>(1));
     unsigned col = tma;
     int k = 1;
-    // four pairs per step (one 8-column store: fewer tensor-memory operations,
-    // each of which the warp must reach together), then two
+    // eight pairs per step (one 16-column store: fewer tensor-memory
+    // operations, each of which the warp must reach together), then four, then
+    // two; the eight-pair steps only over a staged rho' region (with rho' from
+    // global memory they held more loads in flight than the registers allow)
+    for (; (SMEM && !GLD) && k + 7 <= kfast; k += 8) {
+        float x[16];
+        float2 t;
+        t = p1_pair<SMEM, GLD, false, PV, 0, 0>(a0, a1, k, r.la, r.lb, c, kk, D2);
+        x[0] = t.x, x[1] = t.y;
+        t = p1_pair<SMEM, GLD, false, PV, s0, s1>(a0, a1, k, r.la, r.lb, c, kk, D2);
+        x[2] = t.x, x[3] = t.y;
+        t = p1_pair<SMEM, GLD, false, PV, 2 * s0, 2 * s1>(a0, a1, k, r.la, r.lb, c, kk, D2);
+        x[4] = t.x, x[5] = t.y;
+        t = p1_pair<SMEM, GLD, false, PV, 3 * s0, 3 * s1>(a0, a1, k, r.la, r.lb, c, kk, D2);
+        x[6] = t.x, x[7] = t.y;
+        t = p1_pair<SMEM, GLD, false, PV, 4 * s0, 4 * s1>(a0, a1, k, r.la, r.lb, c, kk, D2);
+        x[8] = t.x, x[9] = t.y;
+        t = p1_pair<SMEM, GLD, false, PV, 5 * s0, 5 * s1>(a0, a1, k, r.la, r.lb, c, kk, D2);
+        x[10] = t.x, x[11] = t.y;
+        t = p1_pair<SMEM, GLD, false, PV, 6 * s0, 6 * s1>(a0, a1, k, r.la, r.lb, c, kk, D2);
+        x[12] = t.x, x[13] = t.y;
+        t = p1_pair<SMEM, GLD, false, PV, 7 * s0, 7 * s1>(a0, a1, k, r.la, r.lb, c, kk, D2);
+        x[14] = t.x, x[15] = t.y;
+        if constexpr (ST) tm_st16(col, x);
+        a0 += (Addr)(8 * s0);
+        a1 += (Addr)(8 * s1);
+        col += 16;
+    }
     for (; k + 3 <= kfast; k += 4) {
         const float2 pa = p1_pair<SMEM, GLD, false, PV, 0, 0>(a0, a1, k, r.la, r.lb, c, kk, D2);
         const float2 pb = p1_pair<SMEM, GLD, false, PV, s0, s1>(a0, a1, k + 1, r.la, r.lb, c, kk,
@@ -821,20 +869,22 @@ __device__ __forceinline__ void pass2_pairs(const RowP<SMEM>& r, int act, int kf
 // The fixed-point terms of two pairs (four pixels; pa = pair k, pb = pair k + 1,
 // .x the first pixels, .y the second ones) added into the H words at a0, a1,
 // a0 + S0, a1 + S1 and the L words kAccWords words further on.  v holds
-// P rho' and s2 = 2^12 / D, so x 2^12 = v s2:
+// P rho', s2 = 2^12 / D and sl = 2^32 / D, so x 2^12 = v s2:
 //   t1 = 2^23 + v s2 rounded toward zero   (bits: magic + H, H = floor(x 2^12)),
-//   r  = v s2 - H                          (exact in the FMA, in [0, 1]),
-//   t2 = 2^23 + r 2^20 rounded to nearest  (bits: magic + L).
+//   c  = (2^43 + 2^23) - t1 2^20 = 2^23 - H 2^20        (exact),
+//   t2 = v sl + c rounded to nearest = 2^23 + (x 2^12 - H) 2^20 rounded
+//                                                       (bits: magic + L),
+// the remainder taken from the FMA's exact product v sl.
 template <int S0, int S1>
-__device__ __forceinline__ void fx4(unsigned a0, unsigned a1, float2 pa, float2 pb, float2 s2)
+__device__ __forceinline__ void fx4(unsigned a0, unsigned a1, float2 pa, float2 pb, float2 s2,
+                                    float2 sl)
 {
     const float2 M = make_float2(kFxMagic, kFxMagic);
-    const float2 m1 = make_float2(-1.0f, -1.0f);
-    const float2 sl = make_float2(1048576.0f, 1048576.0f);          // 2^20
+    const float2 m20 = make_float2(-1048576.0f, -1048576.0f);        // -2^20
+    const float2 K = make_float2(0x1p43f + 0x1p23f, 0x1p43f + 0x1p23f);
     const float2 ha = __ffma2_rz(pa, s2, M), hb = __ffma2_rz(pb, s2, M);
-    const float2 ra = __ffma2_rn(pa, s2, __ffma2_rn(ha, m1, M));    // v s2 - H
-    const float2 rb = __ffma2_rn(pb, s2, __ffma2_rn(hb, m1, M));
-    const float2 la = __ffma2_rn(ra, sl, M), lb = __ffma2_rn(rb, sl, M);
+    const float2 la = __ffma2_rn(pa, sl, __ffma2_rn(ha, m20, K));
+    const float2 lb = __ffma2_rn(pb, sl, __ffma2_rn(hb, m20, K));
     asm volatile(
         "red.shared.add.u32 [%0], %4;\n\tred.shared.add.u32 [%1], %5;\n\t"
         "red.shared.add.u32 [%0+%2], %6;\n\tred.shared.add.u32 [%1+%3], %7;\n\t"
@@ -849,24 +899,40 @@ __device__ __forceinline__ void fx4(unsigned a0, unsigned a1, float2 pa, float2 
 }
 
 // Pass 2 of the MLEM tile pass in fixed point: the terms x = P rho' / D of
-// pairs 1 .. kmax (P rho' loaded back from tensor memory, 0 outside each
-// lane's chord) added to the item's two-word accumulator at r.base (H words).
+// pairs 1 .. kmax (P rho' loaded back from tensor memory 16, 8 or 4 values at
+// a time, 0 outside each lane's chord) added to the item's two-word
+// accumulator at r.base (H words).
 template <int TRAV>
 __device__ __forceinline__ void pass2_fx(const RowP<true>& r, int kfast, int kmax, unsigned tma,
-                                         float2 s2)
+                                         float2 s2, float2 sl)
 {
     constexpr int s0 = 4 * pair_step0<TRAV>(), s1 = 4 * pair_step1<TRAV>();
     unsigned a0 = r.base + (unsigned)(4 * pair_d0<TRAV>(1));
     unsigned a1 = r.base + (unsigned)(4 * pair_d1<TRAV>(1));
     unsigned col = tma;
     int k = 1;
+    for (; k + 7 <= kfast; k += 8) {
+        float x[16];
+        tm_ld16(col, x);
+        tm_wait_ld();
+        fx4<s0, s1>(a0, a1, make_float2(x[0], x[1]), make_float2(x[2], x[3]), s2, sl);
+        fx4<s0, s1>(a0 + (unsigned)(2 * s0), a1 + (unsigned)(2 * s1), make_float2(x[4], x[5]),
+                    make_float2(x[6], x[7]), s2, sl);
+        fx4<s0, s1>(a0 + (unsigned)(4 * s0), a1 + (unsigned)(4 * s1), make_float2(x[8], x[9]),
+                    make_float2(x[10], x[11]), s2, sl);
+        fx4<s0, s1>(a0 + (unsigned)(6 * s0), a1 + (unsigned)(6 * s1), make_float2(x[12], x[13]),
+                    make_float2(x[14], x[15]), s2, sl);
+        a0 += (unsigned)(8 * s0);
+        a1 += (unsigned)(8 * s1);
+        col += 16;
+    }
     for (; k + 3 <= kfast; k += 4) {
         float x[8];
         tm_ld8(col, x);
         tm_wait_ld();
-        fx4<s0, s1>(a0, a1, make_float2(x[0], x[1]), make_float2(x[2], x[3]), s2);
+        fx4<s0, s1>(a0, a1, make_float2(x[0], x[1]), make_float2(x[2], x[3]), s2, sl);
         fx4<s0, s1>(a0 + (unsigned)(2 * s0), a1 + (unsigned)(2 * s1), make_float2(x[4], x[5]),
-                    make_float2(x[6], x[7]), s2);
+                    make_float2(x[6], x[7]), s2, sl);
         a0 += (unsigned)(4 * s0);
         a1 += (unsigned)(4 * s1);
         col += 8;
@@ -875,7 +941,7 @@ __device__ __forceinline__ void pass2_fx(const RowP<true>& r, int kfast, int kma
         float x0, x1, x2, x3;
         tm_ld4(col, x0, x1, x2, x3);
         tm_wait_ld();
-        fx4<s0, s1>(a0, a1, make_float2(x0, x1), make_float2(x2, x3), s2);
+        fx4<s0, s1>(a0, a1, make_float2(x0, x1), make_float2(x2, x3), s2, sl);
         a0 += (unsigned)(2 * s0);
         a1 += (unsigned)(2 * s1);
         col += 4;
@@ -977,8 +1043,8 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
             const float invD = 1.0f / D;
             if constexpr (kFx) {
                 q.base += off;
-                const float s = invD * 4096.0f;
-                pass2_fx<TRAV>(q, kfast, kmax, tma, make_float2(s, s));
+                const float s = invD * 4096.0f, sl = invD * 0x1p32f;
+                pass2_fx<TRAV>(q, kfast, kmax, tma, make_float2(s, s), make_float2(sl, sl));
             } else if constexpr (!GRAD) {
                 if (!GLD) q.base += off;
                 const float2 invD2 = make_float2(invD, invD);
