@@ -64,6 +64,9 @@ FMA_OPS_PER_PIXEL = 17
 # dram__bytes_write.sum of one ncu-captured launch over 1e6 events of the
 # 1 mm workload); the traffic grows with the events.
 TILE_PASS_DRAM_B_PER_EVENT = 47.6
+# The same for the accumulator-only tile pass of the 0.5 mm stress workload
+# (one launch over its first 1e6 events; rho' re-read through L1/L2).
+GLD_PASS_DRAM_B_PER_EVENT = 66.0
 
 
 def roofline_basis(device: int):
@@ -507,7 +510,8 @@ def stress_record(workload, inputs, steps: int, warmup_iters: int, with_e2e: boo
                    "l2": "inputs larger than L2", "parallelism": "1 GPU"},
         "roofline": roofline_dict(W, t_pass if pass_ms else None, roof,
                                   "k_tiles (accumulator-only tiles, rho' from global), per launch",
-                                  traffic=None),
+                                  traffic=(GLD_PASS_DRAM_B_PER_EVENT * n
+                                           if workload.name == "stress_05mm" else None)),
         "upload_s": t_upload,
         "e2e": e2e,
         "adjoint_batched_16": {"instances": ADJ_INSTANCES, "events": n_adj, "grid": [350, 250],
