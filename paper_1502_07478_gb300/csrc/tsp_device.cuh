@@ -361,9 +361,13 @@ __device__ __forceinline__ int float_to_index(float x)
 
 // Explicitly rounded operations (never contracted into FMAs), so that the
 // event preparation and the MLEM passes derive bit-identical chords whatever
-// the surrounding code lets the compiler fuse.
+// the surrounding code lets the compiler fuse.  check = false skips the
+// uncertainty tests (exact for an event whose preparation found no row that
+// needed the double-precision decision: the same single-precision values
+// decide the same way); *unsure (when given) records that a row needed it.
 __device__ __forceinline__ Chord row_chord(const Geo& g, const EvSig& es, const float4& ev,
-                                           const Ev64* __restrict__ ev64, int iy)
+                                           const Ev64* __restrict__ ev64, int iy,
+                                           bool check = true, bool* unsure = nullptr)
 {
     Chord c;
     c.y = __fmaf_rn((float)iy, g.dy, g.y0);
@@ -373,7 +377,7 @@ __device__ __forceinline__ Chord row_chord(const Geo& g, const EvSig& es, const 
     c.lo = 0;
     c.count = 0;
     const float rem = __fsub_rn(g.cut2, c.B0);
-    const bool unsure_rem = fabsf(rem) < kRemRel * g.cut2;
+    const bool unsure_rem = check && fabsf(rem) < kRemRel * g.cut2;
     bool unsure_lo = false, unsure_hi = false;
     int a = 0, b = -1;                                // candidate columns [a, b]
     if (rem >= 0.0f) {
@@ -382,14 +386,17 @@ __device__ __forceinline__ Chord row_chord(const Geo& g, const EvSig& es, const 
         const float umax = __fmul_rn(sr, es.inv_sqrt_2iz);
         const float xlo = __fmul_rn(__fsub_rn(__fsub_rn(c.zc, umax), g.z0), g.inv_dz);
         const float xhi = __fmul_rn(__fsub_rn(__fadd_rn(c.zc, umax), g.z0), g.inv_dz);
-        const float coord = (fabsf(c.zc) + umax + fabsf(g.z0)) * g.inv_dz;
-        const float m = kEndRel * (fabsf(xhi) + coord) +
-                        kEndRel * g.cut2 * es.inv_sqrt_2iz * g.inv_dz * rs;
-        unsure_lo = fabsf(xlo - rintf(xlo)) < m;
-        unsure_hi = fabsf(xhi - rintf(xhi)) < m;
+        if (check) {
+            const float coord = (fabsf(c.zc) + umax + fabsf(g.z0)) * g.inv_dz;
+            const float m = kEndRel * (fabsf(xhi) + coord) +
+                            kEndRel * g.cut2 * es.inv_sqrt_2iz * g.inv_dz * rs;
+            unsure_lo = fabsf(xlo - rintf(xlo)) < m;
+            unsure_hi = fabsf(xhi - rintf(xhi)) < m;
+        }
         a = float_to_index(ceilf(xlo));
         b = float_to_index(floorf(xhi));
     }
+    if (unsure && (unsure_rem || unsure_lo || unsure_hi)) *unsure = true;
     if (unsure_rem || unsure_lo || unsure_hi) {
         const Ev64 e = *ev64;
         // (with the context's constants inv_f2 is the literal 1: no z profile)
@@ -446,6 +453,35 @@ __device__ __forceinline__ void row_acb(const Geo& g, const EvSig& es, const flo
     alpha = -2.0f * es.iz * y * c2i;           // aCb slope in u
     beta = 4.0f * g.il * y * t * Dy * c2i;     // aCb at u = 0
     if (g.gR4 != 0.0f) beta -= g.gR4 * c2i * sqrtf(c2i) * Dy;
+}
+
+// Flags kept in the high bits of an event's row count (int2 (first row, rows)):
+// kEvExact, no row of the event's window needed the double-precision window
+// decision (row_chord may skip its uncertainty tests); kEvQPos, Q > 0 over the
+// whole window (reading R5's clip cannot apply).  The event preparation sets
+// them; forms that do not leave them clear, and every reader masks the count.
+constexpr int kEvRowsMask = 0xFFFF;
+constexpr int kEvExact = 1 << 29;
+constexpr int kEvQPos = 1 << 30;
+
+// A lower bound of Q = aCa + 2 oCb over every point of the event's window, in
+// double precision: with y = y~ + Dy, |Dy| <= hy (window half-height) and
+// |u| <= umax (largest chord half-width), each term of row_q's Q is bounded
+// below (the terms in y^2 t^2 and the y^2 part of aCa are >= 0).  The event is
+// flagged when the bound exceeds 1e-3 of the leading term 2 iz R^2 c2i^2, far
+// more than the single-precision error of the row polynomials.
+__device__ __forceinline__ bool q_positive_over_window(const Geo& g, const EvSig& es,
+                                                       const float4& ev)
+{
+    const double iz = es.iz, il = g.il, t = fabs((double)ev.z), c2i = ev.w;
+    const double hy = (double)g.hy_coef / sqrt(c2i) * 1.001 + (double)g.dy;
+    const double umax = sqrt((double)g.cut2) * (double)es.inv_sqrt_2iz + (double)g.dz;
+    const double ymax = fabs((double)ev.x) + hy;
+    const double lead = 2.0 * iz * (double)g.R * g.R * c2i * c2i;
+    double q = lead - 4.0 * il * ymax * (2.0 * t * t + 1.0) * hy * c2i -
+               4.0 * iz * ymax * t * c2i * umax;
+    if (g.gR8 != 0.0f) q -= fabs((double)g.gR8) * t * c2i * sqrt(c2i) * (ymax + hy);
+    return q > 1e-3 * lead;
 }
 
 // Bounding box of the event's window in pixel rows and columns, clipped to the

@@ -99,12 +99,12 @@ __global__ void k_setup(Geo g, Tiling tl, long long n, const float* __restrict__
                                tl.tiles_z * tl.TZ - 1);
             const int ty = iyc / tl.TY, tz = zp / tl.TZ;
             const int oy = ty * tl.TY - tl.HY, zbase = tz * tl.TZ - tl.HZ - tl.zs_off;
-            bool fits = bin_ok;
+            bool fits = bin_ok, unsure = false;
             int first = -1, last = -1;
             unsigned long long cnt = 0;
             for (int r = 0; r < nrows; ++r) {
                 const int iy = iy_lo + r;
-                const Chord c = row_chord(g, es, ev, &e64, iy);
+                const Chord c = row_chord(g, es, ev, &e64, iy, true, &unsure);
                 if (c.count > 0) {
                     if (first < 0) first = iy;
                     last = iy;
@@ -118,7 +118,8 @@ __global__ void k_setup(Geo g, Tiling tl, long long n, const float* __restrict__
                 ++empty;
             } else {
                 pix += cnt;
-                rw = make_int2(first, last - first + 1);
+                rw = make_int2(first, (last - first + 1) | (unsure ? 0 : kEvExact) |
+                                          (q_positive_over_window(g, es, ev) ? kEvQPos : 0));
                 k = fits ? (b * tl.tiles_y + ty) * tl.tiles_z + tz : nbins - 1;
                 if (!fits) ++outl;
             }

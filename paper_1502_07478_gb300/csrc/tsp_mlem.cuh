@@ -117,7 +117,8 @@ __device__ __forceinline__ void row_idle(RowK<SMEM>& r, RowG& rg)
 // counted).
 template <int TRAV, int LMAX, bool GRAD, bool SMEM, bool GLD>
 __device__ __forceinline__ void make_row(const Geo& g, const EvSig& es, const float4& ev,
-                                         const Ev64* ev64, int iy, bool valid_row, const Frame* fp,
+                                         const Ev64* ev64, int iy, bool valid_row, int evflags,
+                                         const Frame* fp,
                                          const float* base, const float* gimg, RowK<SMEM>& r,
                                          RowG& rg, BlockSums* bs)
 {
@@ -128,7 +129,7 @@ __device__ __forceinline__ void make_row(const Geo& g, const EvSig& es, const fl
     const Frame f = *fp;
     float Qc = 0.0f, gam2 = 0.0f;
     if (valid_row) {
-        c = row_chord(g, es, ev, ev64, iy);
+        c = row_chord(g, es, ev, ev64, iy, !(evflags & kEvExact));
         lo = c.lo;
         hi = c.lo + c.count - 1;
         if (c.count > 0 && (iy < f.oy || iy >= f.oy + f.rh)) {
@@ -144,8 +145,11 @@ __device__ __forceinline__ void make_row(const Geo& g, const EvSig& es, const fl
         }
         if (hi >= lo) {
             row_q(g, es, ev, c, Qc, gam2);
-            // Reading R5: P = 0 where Q <= 0.  Q is linear along the chord, so
-            // the pixels with Q > 0 form a sub-range; keep only that.
+        }
+        // Reading R5: P = 0 where Q <= 0.  Q is linear along the chord, so the
+        // pixels with Q > 0 form a sub-range; keep only that (unless the event
+        // preparation bounded Q > 0 over the whole window).
+        if (hi >= lo && !(evflags & kEvQPos)) {
             const float ulo = fmaf((float)lo, g.dz, g.z0) - c.zc;
             const float uhi = fmaf((float)hi, g.dz, g.z0) - c.zc;
             const float Qlo = fmaf(gam2, ulo, Qc), Qhi = fmaf(gam2, uhi, Qc);
@@ -963,7 +967,9 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
     // the MLEM pass over a staged region accumulates in fixed point (fx4)
     constexpr bool kFx = (MODE == kMlem) && SMEM && !GLD;
     const float4 ev = evs.geo[e];
-    const int2 rws = evs.rows[e];
+    int2 rws = evs.rows[e];
+    const int evflags = rws.y & ~kEvRowsMask;
+    rws.y &= kEvRowsMask;
     RowK<SMEM> r;
     RowG rg;
     // Rows are paired around the middle of the window (lane-row 2k -> mid - k,
@@ -977,7 +983,7 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
     const int ri = (rowi & 1) ? mid + k + 1 : mid - k;
     // KZ: the event's own sigma_z (z profile); else the context's constants
     make_row<TRAV, LMAX, GRAD, SMEM, GLD>(g, KZ ? ev_sig(g, ev) : geo_sig(g), ev, evs.geo64 + e,
-                                          rws.x + ri, ri >= 0 && ri < rws.y, f,
+                                          rws.x + ri, ri >= 0 && ri < rws.y, evflags, f,
                                           GLD ? acc_base : rp_base, rp_base, r, rg, bs);
     float D = 0.0f, Ez = 0.0f, El = 0.0f;
     float P[4];

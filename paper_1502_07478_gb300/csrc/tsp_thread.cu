@@ -21,7 +21,8 @@ k_thread_events(Geo g, EventsView evs, int n, const float* __restrict__ rhop,
     unsigned long long used = 0, qclip = 0;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         const float4 ev = evs.geo[j];
-        const int2 rws = evs.rows[j];
+        int2 rws = evs.rows[j];
+        rws.y &= kEvRowsMask;
         const EvSig es = ev_sig(g, ev);
         float D = 0.0f, invD = 0.0f;
         for (int pass = 0; pass < 2; ++pass) {
