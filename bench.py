@@ -63,7 +63,7 @@ FMA_OPS_PER_PIXEL = 17
 # DRAM bytes per event of one MLEM tile pass (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu-captured launch over 1e6 events of the
 # 1 mm workload); the traffic grows with the events.
-TILE_PASS_DRAM_B_PER_EVENT = 47.6
+TILE_PASS_DRAM_B_PER_EVENT = 47.7
 # The same for the accumulator-only tile pass of the 0.5 mm stress workload
 # (one launch over its first 1e6 events; rho' re-read through L1/L2).
 GLD_PASS_DRAM_B_PER_EVENT = 66.0
