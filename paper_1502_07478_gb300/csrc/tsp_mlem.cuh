@@ -10,18 +10,22 @@
 // image row of the event's window (or one side of it):
 //   pass 1: walk the lane's chord of the ellipse outward from its centre,
 //           evaluate P (Eq. kernel) in the log2 domain (one rsqrt and one ex2
-//           per pixel, two pixels per packed f32x2 instruction), keep P in the
-//           lane's tensor memory and accumulate D_j = sum P rho' (the
-//           denominator of Eq. iter); warp shuffles and a named barrier
-//           reduce D_j over the group;
-//   pass 2: add P / D_j into the shared accumulator (shared-memory atomics: two
-//           groups may touch the same pixel).
+//           per pixel, two pixels per packed f32x2 instruction), keep P rho'
+//           (P in the adjoint pass and in the accumulator-only tiles) in the
+//           lane's tensor memory and accumulate
+//           D_j = sum P rho' (the denominator of Eq. iter); warp shuffles and a
+//           named barrier reduce D_j over the group;
+//   pass 2: add the terms P rho' / D_j in [0, 1] into the item's two-word
+//           fixed-point accumulator with native integer shared-memory atomics
+//           (two groups may touch the same pixel; the layout constants in
+//           tsp_device.cuh state the split and its bounds).  The adjoint pass
+//           and the accumulator-only tiles add P / D_j as floats.
 // A warp's lanes hold 32 distinct rows (paired around the window's middle);
 // with the sheared frame and a row stride of 1 mod 32 words their accesses at
 // each step fall in distinct banks.
 // At the end of the item the accumulator is flushed to the global
-// back-projection A with one atomic add per touched pixel; the finalize kernel
-// then forms rho <- rho * A.
+// back-projection A with one atomic add per touched pixel (the fixed-point sum
+// divided by the pixel's rho'); the finalize kernel then forms rho <- rho * A.
 //
 // Relative to the paper's GPU design (one warp per event over its bounding
 // box, rho read through the texture cache, Sec. 4.2): lanes own chords of the
