@@ -67,6 +67,10 @@ TILE_PASS_DRAM_B_PER_EVENT = 47.7
 # The same for the accumulator-only tile pass of the 0.5 mm stress workload
 # (one launch over its first 1e6 events; rho' re-read through L1/L2).
 GLD_PASS_DRAM_B_PER_EVENT = 66.0
+# Warp instructions issued per in-window pixel evaluation (smsp__inst_executed.sum
+# / W of the same captures): the pass is issue-bound, so this is its tracked cost.
+TILE_PASS_WARP_INST_PER_EVAL = 1.07
+GLD_PASS_WARP_INST_PER_EVAL = 1.17
 
 
 def roofline_basis(device: int):
@@ -83,7 +87,7 @@ def roofline_basis(device: int):
                      f"FMA clk) per pixel evaluation"}
 
 
-def roofline_dict(W, t_pass, basis, kernel, traffic=None):
+def roofline_dict(W, t_pass, basis, kernel, traffic=None, inst_per_eval=None):
     """The bench line's roofline object for a pass of W pixel evaluations
     taking t_pass seconds (None when not timed)."""
     achieved = W / t_pass if t_pass else None
@@ -94,6 +98,7 @@ def roofline_dict(W, t_pass, basis, kernel, traffic=None):
             "traffic": traffic,
             "traffic_basis": ("ncu DRAM bytes of one 1e6-event launch, scaled by events"
                               if traffic is not None else None),
+            "warp_inst_per_eval": inst_per_eval,
             "kernel": kernel, "pixel_evals_per_launch": W,
             "launch_ms": t_pass * 1e3 if t_pass else None,
             "peak_basis": basis["basis"]}
@@ -511,7 +516,9 @@ def stress_record(workload, inputs, steps: int, warmup_iters: int, with_e2e: boo
         "roofline": roofline_dict(W, t_pass if pass_ms else None, roof,
                                   "k_tiles (accumulator-only tiles, rho' from global), per launch",
                                   traffic=(GLD_PASS_DRAM_B_PER_EVENT * n
-                                           if workload.name == "stress_05mm" else None)),
+                                           if workload.name == "stress_05mm" else None),
+                                  inst_per_eval=(GLD_PASS_WARP_INST_PER_EVAL
+                                                 if workload.name == "stress_05mm" else None)),
         "upload_s": t_upload,
         "e2e": e2e,
         "adjoint_batched_16": {"instances": ADJ_INSTANCES, "events": n_adj, "grid": [350, 250],
@@ -706,7 +713,9 @@ def main():
         W, t_pass, roofline_basis(local),
         ("k_tiles" if args.variant == "tiles" else "k_thread_events") + " (MLEM pass, per launch)",
         traffic=(TILE_PASS_DRAM_B_PER_EVENT * n
-                 if workload.name == "paper_1mm" and args.variant == "tiles" else None))
+                 if workload.name == "paper_1mm" and args.variant == "tiles" else None),
+        inst_per_eval=(TILE_PASS_WARP_INST_PER_EVAL
+                       if workload.name == "paper_1mm" and args.variant == "tiles" else None))
 
     e2e = None
     if not args.no_e2e:
