@@ -334,6 +334,9 @@ long long item_events(long long placed, int items_per_sm, int sms)
 
 std::vector<int4> tile_items(const tsp_ctx* c, long long E, int w)
 {
+    // the fixed-point accumulator's sums are exact for items of at most
+    // kItemMaxEvents events (tsp_device.cuh)
+    E = std::max(1ll, std::min(E, (long long)kItemMaxEvents));
     std::vector<int4> items;
     const int nb = (int)c->bin_cnt.size() - 1;     // the last bin holds the outliers
     for (long long k = 0;; ++k) {
