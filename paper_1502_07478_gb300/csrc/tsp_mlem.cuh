@@ -1226,7 +1226,7 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
         float* s_rp = smem + kPadFloats;
         float* s_acc = GLD ? s_rp : s_rp + region + 2 * kPadFloats;
         // the L words of the fixed-point accumulator (MLEM over a staged region)
-        unsigned* s_accL = reinterpret_cast<unsigned*>(s_acc) + kAccWords;
+        unsigned* s_accL = GLD ? nullptr : reinterpret_cast<unsigned*>(s_acc) + kAccWords;
         float* part = (GLD ? s_acc : s_acc + kAccWords) + region + kPadFloats + grp * (2 * 3 * G);
         int parity = 0;
         const Frame f = tile_frame(g, tl, item.x);
