@@ -464,24 +464,25 @@ constexpr int kEvRowsMask = 0xFFFF;
 constexpr int kEvExact = 1 << 29;
 constexpr int kEvQPos = 1 << 30;
 
-// A lower bound of Q = aCa + 2 oCb over every point of the event's window, in
-// double precision: with y = y~ + Dy, |Dy| <= hy (window half-height) and
-// |u| <= umax (largest chord half-width), each term of row_q's Q is bounded
-// below (the terms in y^2 t^2 and the y^2 part of aCa are >= 0).  The event is
-// flagged when the bound exceeds 1e-3 of the leading term 2 iz R^2 c2i^2, far
-// more than the single-precision error of the row polynomials.
+// A lower bound of Q = aCa + 2 oCb over every point of the event's window:
+// with y = y~ + Dy, |Dy| <= hy (window half-height) and |u| <= umax (largest
+// chord half-width), each term of row_q's Q is bounded below (the terms in
+// y^2 t^2 and the y^2 part of aCa are >= 0).  The event is flagged when the
+// bound exceeds 1e-3 of its leading term 2 iz R^2 c2i^2: that margin is three
+// orders above the single-precision rounding of this bound and of the row
+// polynomials, so single precision suffices here.
 __device__ __forceinline__ bool q_positive_over_window(const Geo& g, const EvSig& es,
                                                        const float4& ev)
 {
-    const double iz = es.iz, il = g.il, t = fabs((double)ev.z), c2i = ev.w;
-    const double hy = (double)g.hy_coef / sqrt(c2i) * 1.001 + (double)g.dy;
-    const double umax = sqrt((double)g.cut2) * (double)es.inv_sqrt_2iz + (double)g.dz;
-    const double ymax = fabs((double)ev.x) + hy;
-    const double lead = 2.0 * iz * (double)g.R * g.R * c2i * c2i;
-    double q = lead - 4.0 * il * ymax * (2.0 * t * t + 1.0) * hy * c2i -
-               4.0 * iz * ymax * t * c2i * umax;
-    if (g.gR8 != 0.0f) q -= fabs((double)g.gR8) * t * c2i * sqrt(c2i) * (ymax + hy);
-    return q > 1e-3 * lead;
+    const float t = fabsf(ev.z), c2i = ev.w;
+    const float hy = g.hy_coef * rsqrtf(c2i) * 1.001f + g.dy;
+    const float umax = sqrtf(g.cut2) * es.inv_sqrt_2iz + g.dz;
+    const float ymax = fabsf(ev.x) + hy;
+    const float lead = 2.0f * es.iz * g.R * g.R * c2i * c2i;
+    float q = lead - 4.0f * g.il * ymax * (2.0f * t * t + 1.0f) * hy * c2i -
+              4.0f * es.iz * ymax * t * c2i * umax;
+    if (g.gR8 != 0.0f) q -= fabsf(g.gR8) * t * c2i * sqrtf(c2i) * (ymax + hy);
+    return q > 1e-3f * lead;
 }
 
 // Bounding box of the event's window in pixel rows and columns, clipped to the
