@@ -195,10 +195,23 @@ def cpu_baseline(workload, target_s: float = 12.0):
     oracle.mlem(st, ev, 1, s=s)
     dt = time.perf_counter() - t0
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    # the same oracle on one thread, over a sample 1/cores as long (about as many seconds)
+    n1 = max(500, n // max(1, cores))
+    st1 = _replace(st, n_threads=1)
+    t0 = time.perf_counter()
+    oracle.mlem(st1, ev_first(workload, n1), 1, s=s)
+    dt1 = time.perf_counter() - t0
     return {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"1 iteration of Eq. iter over the first {n} events of the "
                       f"{workload.name} workload ({workload.ny}x{workload.nz} grid), FP64, "
-                      f"{dt:.1f} s"}
+                      f"{dt:.1f} s",
+            "single_thread": {"value": n1 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"the first {n1} events, {dt1:.1f} s"}}
+
+
+def ev_first(workload, n):
+    """The first n events of the workload (the seed's first n draws)."""
+    return _replace(workload, n_events=n).events()
 
 
 def _replace(w, **kw):
