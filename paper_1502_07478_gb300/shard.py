@@ -8,6 +8,9 @@ each, every rank holding the same image) advances by one iteration as:
   2. the ranks' back-projections are summed (an all-reduce, e.g. NCCL),
   3. every rank applies the summed back-projection (``Recon.apply_update``,
      tsp_apply_update), so the images stay identical.
+The log-likelihood and its gradients shard the same way (``sharded_loglik_grad``):
+one all-reduce of g_rho and one of (L, g_sigma), plus the image terms that
+every rank would otherwise count once each.
 This module only orders those calls; the kernels run in libtsp and the sum in
 the collective library.
 """
@@ -27,3 +30,31 @@ def sharded_iterate(recon, n_iter: int, all_reduce: Callable, buf=None) -> Optio
         all_reduce(buf)
         recon.apply_update(buf)
     return buf
+
+
+def sharded_loglik_grad(recon, all_reduce: Callable, world_size: int):
+    """The log-likelihood and its gradients over the whole event list, from
+    ``recon`` holding this rank's share (every rank the same image and
+    resolution).  With L = sum_j log D_j - sum_i s_i rho_i,
+    g_rho = s (sum_j P_j/D_j - 1) and g_sigma = sum_j (...)/D_j
+    (``Recon.loglik_grad``), the event sums add over ranks and the image
+    terms are counted once:
+        L       = sum_r L_r       + (K - 1) sum_i s_i rho_i,
+        g_rho   = sum_r g_rho,r   + (K - 1) s,
+        g_sigma = sum_r g_sigma,r,
+    for K ranks: one all-reduce of g_rho and one of (L, g_sigma).
+    ``all_reduce(t)`` must sum a tensor in place over the ranks.  Returns
+    (L, g_rho, g_sigma) on every rank."""
+    import numpy as np
+    import torch
+    L, g, gs = recon.loglik_grad()
+    extra = int(world_size) - 1
+    s = recon.compute_sensitivity()
+    S = float(recon.read_image(which=1).double().sum())
+    all_reduce(g)
+    if extra:
+        g += extra * s.to(g.dtype)
+    v = torch.tensor([L, gs[0], gs[1]], dtype=torch.float64, device=g.device)
+    all_reduce(v)
+    v = v.cpu().numpy()
+    return float(v[0]) + extra * S, g, np.array(v[1:])

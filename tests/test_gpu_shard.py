@@ -174,3 +174,36 @@ def test_wait_times_out_then_completes():
     st = r.stats()
     assert st["sum_s_rho"] == pytest.approx(st["n_used"], rel=1e-5)
     r.close()
+
+
+def test_sharded_loglik_grad_parts_add_up():
+    """The log-likelihood and gradients of two contexts on the two halves of the
+    events combine as shard.sharded_loglik_grad combines them (event sums add,
+    the image terms once) into those of one context over all events."""
+    import torch
+    w = make_workload("small_5mm")
+    ev = w.events()
+    rho = np.random.Generator(np.random.PCG64(5)).uniform(0.5, 2.0, (w.ny, w.nz)).astype(
+        np.float32)
+    half = len(ev[0]) // 2
+    parts = []
+    for sl in (slice(0, half), slice(half, None)):
+        c = _recon(w)
+        c.upload_events(*[e[sl] for e in ev])
+        c.set_image(rho)
+        L, g, gs = c.loglik_grad()
+        parts.append((L, g.double(), gs))
+        s = c.compute_sensitivity().double()
+        S = float(c.read_image(which=1).double().sum())
+        c.close()
+    whole = _recon(w)
+    whole.upload_events(*ev)
+    whole.set_image(rho)
+    L, g, gs = whole.loglik_grad()
+    whole.close()
+    L_sh = parts[0][0] + parts[1][0] + S
+    g_sh = parts[0][1] + parts[1][1] + s
+    gs_sh = parts[0][2] + parts[1][2]
+    assert L_sh == pytest.approx(L, rel=1e-6)
+    assert float(torch.linalg.norm(g_sh - g.double()) / torch.linalg.norm(g.double())) <= 1e-5
+    np.testing.assert_allclose(gs_sh, gs, rtol=1e-5)

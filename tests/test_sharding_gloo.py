@@ -146,3 +146,75 @@ def test_sharded_loop_equals_whole():
     rho, _ = oracle.mlem(Setup.from_workload(w), ev, n_iter)
     for r in (0, 1):
         np.testing.assert_allclose(got[r], rho, rtol=1e-12, atol=1e-300)
+
+
+class _OracleAdjShard:
+    """Stand-in for a Recon holding one rank's share of the events, with the
+    FP64 oracle's log-likelihood and gradients (Recon.loglik_grad's quantities)."""
+
+    def __init__(self, st, events, s, rho):
+        import oracle
+        self._oracle = oracle
+        self.st, self.events, self.s, self.rho = st, events, s, rho
+
+    def loglik_grad(self):
+        L, g, gs = self._oracle.loglik_grad(self.st, self.events, self.rho, s=self.s)
+        return L, torch.from_numpy(np.asarray(g).reshape(self.rho.shape).copy()), np.asarray(gs)
+
+    def compute_sensitivity(self):
+        return torch.from_numpy(np.asarray(self.s).reshape(self.rho.shape).copy())
+
+    def read_image(self, which=0):
+        return torch.from_numpy(self.rho * (np.asarray(self.s).reshape(self.rho.shape)
+                                            if which == 1 else 1.0))
+
+
+def _adj_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    from oracle import Setup
+    from paper_1502_07478_gb300.shard import sharded_loglik_grad
+    from synth import make_workload
+    w = make_workload("small_5mm", n_events=3000)
+    ev = [e.astype(np.float64) for e in w.events()]
+    st = Setup.from_workload(w, n_threads=1)
+    s = oracle.sensitivity(st)
+    rho = np.random.Generator(np.random.PCG64(11)).uniform(0.5, 2.0, (w.ny, w.nz))
+    cut = len(ev[0]) // 3
+    mine = [e[:cut] for e in ev] if rank == 0 else [e[cut:] for e in ev]
+    L, g, gs = sharded_loglik_grad(_OracleAdjShard(st, mine, s, rho), dist.all_reduce, world)
+    q.put((rank, L, g.numpy(), gs))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_loglik_grad_equals_whole():
+    """paper_1502_07478_gb300.shard.sharded_loglik_grad over two gloo ranks with
+    uneven shares: L, g_rho and g_sigma of the whole list on both ranks (the
+    image terms of L and g_rho counted once)."""
+    import oracle
+    from oracle import Setup
+    from synth import make_workload
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_adj_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = {r: (L, g, gs) for r, L, g, gs in (q.get(timeout=300) for _ in range(2))}
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    w = make_workload("small_5mm", n_events=3000)
+    ev = [e.astype(np.float64) for e in w.events()]
+    st = Setup.from_workload(w)
+    rho = np.random.Generator(np.random.PCG64(11)).uniform(0.5, 2.0, (w.ny, w.nz))
+    L, g, gs = oracle.loglik_grad(st, ev, rho)
+    for r in (0, 1):
+        Lr, gr, gsr = got[r]
+        assert Lr == pytest.approx(L, rel=1e-12)
+        np.testing.assert_allclose(gr.ravel(), np.asarray(g).ravel(), rtol=1e-10,
+                                   atol=1e-12 * float(np.abs(g).max()))
+        np.testing.assert_allclose(gsr, gs, rtol=1e-10)
