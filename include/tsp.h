@@ -29,8 +29,9 @@
  *    tsp_destroy().
  *  - Error paths can be exercised without a device fault: the environment
  *    variable TSP_SIM_FAULT = oom (device allocations fail: TSP_ENOMEM),
- *    launch (kernel launches fail before anything is enqueued: TSP_ECUDA) or
- *    nan_event (each uploaded chunk gets a NaN z_u: TSP_EINVAL) simulates that
+ *    launch (kernel launches fail before anything is enqueued: TSP_ECUDA),
+ *    nan_event (each uploaded chunk gets a NaN z_u: TSP_EINVAL) or timeout
+ *    (tsp_wait gives up at once: TSP_ETIMEOUT) simulates that
  *    failure at every site it reaches while it is set.  A context whose call
  *    failed this way can still be destroyed, and new contexts work once the
  *    variable is unset.

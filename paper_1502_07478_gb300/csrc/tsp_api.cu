@@ -981,6 +981,9 @@ int tsp_wait(tsp_ctx* c, void* stream, int timeout_ms)
     if (timeout_ms < 0) return fail(c, TSP_EINVAL, "timeout_ms < 0");
     DeviceGuard dg(c->dev);
     TSP_CUDA(c, cudaEventRecord(c->wait_ev, (cudaStream_t)stream));
+    if (sim_fault() == kSimTimeout)
+        return fail(c, TSP_ETIMEOUT, "the work enqueued on the stream did not finish within " +
+                                         std::to_string(timeout_ms) + " ms (simulated)");
     const auto t0 = std::chrono::steady_clock::now();
     for (;;) {
         const cudaError_t e = cudaEventQuery(c->wait_ev);

@@ -430,6 +430,7 @@ int sim_fault()
     if (!std::strcmp(v, "oom")) return kSimOom;
     if (!std::strcmp(v, "launch")) return kSimLaunch;
     if (!std::strcmp(v, "nan_event")) return kSimNan;
+    if (!std::strcmp(v, "timeout")) return kSimTimeout;
     return kSimNone;
 }
 

@@ -25,8 +25,10 @@ bool cinv_valid(const tsp_params& p);
 //              cudaErrorLaunchOutOfResources (TSP_ECUDA)
 //   nan_event  every uploaded chunk gets a NaN in its first z_u after the copy
 //              (the event preparation rejects the upload: TSP_EINVAL)
+//   timeout    the bounded wait (tsp_wait) gives up at once, as when the
+//              enqueued work outlasts the limit (TSP_ETIMEOUT)
 // Unset or any other value: no fault.
-enum SimFault : int { kSimNone = 0, kSimOom = 1, kSimLaunch = 2, kSimNan = 3 };
+enum SimFault : int { kSimNone = 0, kSimOom = 1, kSimLaunch = 2, kSimNan = 3, kSimTimeout = 4 };
 int sim_fault();
 
 // The error a launch helper returns under TSP_SIM_FAULT=launch, else success.

@@ -1,8 +1,9 @@
 """Error paths of the C ABI under host-side fault injection (TSP_SIM_FAULT).
 
 No device fault is made: the library simulates an exhausted allocator
-(``oom``), a failed kernel launch before anything is enqueued (``launch``) or
-corrupt input (``nan_event``, a NaN written into the uploaded z_u).  Each test
+(``oom``), a failed kernel launch before anything is enqueued (``launch``),
+corrupt input (``nan_event``, a NaN written into the uploaded z_u) or a
+bounded wait that gives up (``timeout``).  Each test
 checks the return code and message, that the failed context can still be
 destroyed without leaking device memory, and that a fresh context works
 afterwards.
@@ -171,3 +172,24 @@ def test_batch_oom_at_create(small, fault):
     b.iterate(1)
     assert b.stats(1)["sum_s_rho"] == pytest.approx(b.stats(1)["n_used"], rel=2e-6)
     b.close()
+
+
+def test_simulated_timeout(small, fault):
+    """TSP_SIM_FAULT=timeout: tsp_wait returns TSP_ETIMEOUT at once with its
+    message; the queued work still completes and the context stays usable."""
+    from paper_1502_07478_gb300 import Recon
+    from paper_1502_07478_gb300._lib import TSP_ETIMEOUT, lib
+    w, ev = small
+    r = Recon.from_workload(w)
+    r.upload_events(*ev)
+    r.iterate(1)
+    fault("timeout")
+    assert r.wait(60_000) is False
+    assert lib().tsp_wait(r._h, None, 60_000) == TSP_ETIMEOUT
+    assert b"simulated" in lib().tsp_last_error(r._h)
+    fault(None)
+    assert r.wait(60_000) is True
+    r.iterate(2)
+    st = r.stats()
+    assert st["sum_s_rho"] == pytest.approx(st["n_used"], rel=2e-6)
+    r.close()
