@@ -93,6 +93,11 @@ typedef struct {
     int64_t n_clipped;   /* window pixels outside the staged tile region in the
                             last pass (always 0 unless the library is faulty) */
     double sum_s_rho;    /* sum_l s_l rho_l of the current image */
+    int64_t dbg_violation; /* a library built with TSP_DEBUG_CHECKS: the first
+                            shared-memory access of a tile pass outside its block's
+                            window since the context was created, as
+                            (site << 32) | (byte offset + 1), the access skipped;
+                            0 if none, and always 0 in a release build */
 } tsp_stats_t;
 
 /* Create a context for one reconstruction.  Validates params (TSP_EINVAL) and

@@ -38,7 +38,7 @@ class Stats(C.Structure):
     _fields_ = [("n_events", C.c_int64), ("n_used", C.c_int64), ("n_empty", C.c_int64),
                 ("n_outliers", C.c_int64), ("n_window", C.c_int64), ("iterations", C.c_int64),
                 ("launches", C.c_int64), ("n_qbad", C.c_int64), ("n_clipped", C.c_int64),
-                ("sum_s_rho", C.c_double)]
+                ("sum_s_rho", C.c_double), ("dbg_violation", C.c_int64)]
 
 
 class Schedule(C.Structure):
@@ -102,14 +102,17 @@ _lib = None
 
 
 def lib():
-    """The loaded libtsp (raises if it has not been built)."""
+    """The loaded libtsp (raises if it has not been built).  The environment
+    variable TSP_LIBRARY names another build of it to load instead (the
+    bounds-checking build of ``build(debug=True)``)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB):
-            raise RuntimeError(f"libtsp is not built ({LIB} missing); run "
+        path = os.environ.get("TSP_LIBRARY") or LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libtsp is not built ({path} missing); run "
                                "`python -m paper_1502_07478_gb300.build` or "
                                "`__graft_entry__.build()` first")
-        L = C.CDLL(LIB)
+        L = C.CDLL(path)
         for name, res, args in SIGNATURES:
             f = getattr(L, name)
             f.restype = res

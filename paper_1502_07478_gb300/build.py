@@ -1,8 +1,9 @@
 """Build libtsp.so (the CUDA library behind include/tsp.h) in-tree.
 
 Each .cu file under csrc/ is compiled for sm_103a in parallel, then linked into
-paper_1502_07478_gb300/_build/libtsp.so.  Usage: ``python -m
-paper_1502_07478_gb300.build [--force] [--verbose]``.
+paper_1502_07478_gb300/_build/libtsp.so (``--debug``: the bounds-checking build
+into _build_debug/).  Usage: ``python -m paper_1502_07478_gb300.build [--force]
+[--verbose] [--debug]``.
 """
 from __future__ import annotations
 
@@ -18,6 +19,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtsp.so")
+# the bounds-checking build (TSP_DEBUG_CHECKS), loaded through TSP_LIBRARY
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "libtsp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,24 +41,27 @@ def _deps():
         glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def _up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def _up_to_date(lib: str) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    if not force and _up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), debug: bool = False) -> str:
+    """Compile and link libtsp; debug=True builds the bounds-checking variant
+    (TSP_DEBUG_CHECKS) into its own directory instead.  Returns the library path."""
+    build_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    if not force and _up_to_date(lib):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, *ARCH,
-             *extra_flags]
+             *(["-DTSP_DEBUG_CHECKS"] if debug else []), *extra_flags]
     if verbose:
         flags += ["-Xptxas", "-v"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         cmd = [nvcc(), "-c", src, "-o", obj, *flags]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -67,15 +74,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     if verbose:
         for _, log in results:
             sys.stderr.write(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc(), "-shared", "-o", tmp, *[o for o, _ in results], *ARCH, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="--verbose" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv,
+                debug="--debug" in sys.argv))

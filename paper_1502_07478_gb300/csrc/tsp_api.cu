@@ -778,6 +778,7 @@ int tsp_stats(tsp_ctx* c, tsp_stats_t* out, void* stream)
     out->n_qbad = (int64_t)h.n_qclip;
     out->n_clipped = (int64_t)h.n_lclip;
     out->sum_s_rho = h.sum_rhop;
+    out->dbg_violation = (int64_t)h.dbg;
     return TSP_OK;
 }
 

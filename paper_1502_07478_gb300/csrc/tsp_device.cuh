@@ -208,7 +208,10 @@ struct Accum {
     unsigned long long n_used;   // events with D > 0
     unsigned long long n_qclip;  // in-window pixels dropped because Q <= 0
     unsigned long long n_lclip;  // chord pixels beyond the lane capacity (must stay 0)
-    unsigned long long pad0;
+    unsigned long long dbg;      // TSP_DEBUG_CHECKS builds: the first shared-memory access
+                                 // outside a block's dynamic window since the context was
+                                 // created (not cleared per pass), as
+                                 // (site << 32) | (byte offset from the window + 1); else 0
     double sum_logD;             // sum_j log D_j
     double g_iz;                 // sum_j (1/D_j) sum_i rho'_i P_ji dlogP/d(iz)
     double g_il;                 // sum_j (1/D_j) sum_i rho'_i P_ji dlogP/d(il)
@@ -216,6 +219,30 @@ struct Accum {
     int queue;                   // persistent-kernel work counter
     int pad1[3];
 };
+
+// Bounds checks of a TSP_DEBUG_CHECKS build (a substitute for a memory checker):
+// every shared-memory access of the tile passes' pixel loops is tested against
+// the block's dynamic shared-memory window; an access outside it is skipped and
+// the first one is recorded in tsp_dbg_word (per block), which the kernel
+// copies to Accum::dbg at its end.  Sites: 1 pass-1 rho' load, 2 pass-2
+// fixed-point add, 3 pass-2 float add, 4 scalar pass load, 5 scalar pass add.
+// Release builds compile the checks away (tsp_sh_ok is the literal true).
+#ifdef TSP_DEBUG_CHECKS
+extern __shared__ float4 tsp_dyn_smem[];
+__shared__ unsigned long long tsp_dbg_word;
+
+__device__ __forceinline__ bool tsp_sh_ok(unsigned a, unsigned bytes, int site)
+{
+    const unsigned lo = (unsigned)__cvta_generic_to_shared(tsp_dyn_smem);
+    unsigned n;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(n));
+    if (a >= lo && a - lo + bytes <= n) return true;
+    atomicCAS(&tsp_dbg_word, 0ull, ((unsigned long long)site << 32) | (unsigned)(a - lo + 1u));
+    return false;
+}
+#else
+__device__ __forceinline__ constexpr bool tsp_sh_ok(unsigned, unsigned, int) { return true; }
+#endif
 
 // Double-precision event geometry (y~, z~, tan theta~, 1 + tan^2), 32-byte
 // aligned so that one event is one 32-byte load.

@@ -286,6 +286,9 @@ __device__ __forceinline__ float load_acc(const RowK<SMEM>& r, int lim, int m, f
 {
     float v;
     if constexpr (SMEM) {
+#ifdef TSP_DEBUG_CHECKS
+        if (m < lim && !tsp_sh_ok(r.base + OFF, 4, 4)) return 0.0f;
+#endif
         asm(
             "{\n\t.reg .pred q;\n\t"
             "setp.lt.s32 q, %2, %3;\n\t"
@@ -329,6 +332,9 @@ template <bool SMEM, int OFF>
 __device__ __forceinline__ void red_add(const RowK<SMEM>& r, int lim, int m, float v)
 {
     if constexpr (SMEM) {
+#ifdef TSP_DEBUG_CHECKS
+        if (m < lim && !tsp_sh_ok(r.base + OFF, 4, 5)) return;
+#endif
         asm volatile(
             "{\n\t.reg .pred q;\n\t"
             "setp.lt.s32 q, %0, %1;\n\t"
@@ -638,6 +644,9 @@ __device__ __forceinline__ float ld_rhop(typename std::conditional<SMEM && !GLD,
         else
             asm("ld.global.nc.f32 %0, [%1+%2];" : "=f"(v) : "l"(a), "n"(OFF));
     } else if constexpr (SMEM) {
+#ifdef TSP_DEBUG_CHECKS
+        if ((!PRED || k <= lim) && !tsp_sh_ok(a + (unsigned)OFF, 4, 1)) return 0.0f;
+#endif
         if constexpr (PRED)
             asm volatile("{\n\t.reg .pred q;\n\tsetp.le.s32 q, %1, %2;\n\tmov.b32 %0, 0;\n\t"
                          "@q ld.shared.f32 %0, [%3+%4];\n\t}"
@@ -797,6 +806,11 @@ __device__ __forceinline__ void red4(Addr a0, Addr a1, int k, int la, int lb, in
 {
     if constexpr (SMEM) {
         (void)k, (void)la, (void)lb, (void)act;
+#ifdef TSP_DEBUG_CHECKS
+        if (!(tsp_sh_ok(a0, 4, 3) && tsp_sh_ok(a1, 4, 3) && tsp_sh_ok(a0 + (unsigned)S0, 4, 3) &&
+              tsp_sh_ok(a1 + (unsigned)S1, 4, 3)))
+            return;
+#endif
         asm volatile(
             "red.shared.add.f32 [%0], %4;\n\tred.shared.add.f32 [%1], %5;\n\t"
             "red.shared.add.f32 [%0+%2], %6;\n\tred.shared.add.f32 [%1+%3], %7;"
@@ -893,6 +907,16 @@ __device__ __forceinline__ void fx4(unsigned a0, unsigned a1, float2 pa, float2 
     const float2 ha = __ffma2_rz(pa, s2, M), hb = __ffma2_rz(pb, s2, M);
     const float2 la = __ffma2_rn(pa, sl, __ffma2_rn(ha, m20, K));
     const float2 lb = __ffma2_rn(pb, sl, __ffma2_rn(hb, m20, K));
+#ifdef TSP_DEBUG_CHECKS
+    {
+        constexpr unsigned C = 4u * kAccWords;
+        if (!(tsp_sh_ok(a0, 4, 2) && tsp_sh_ok(a1, 4, 2) && tsp_sh_ok(a0 + (unsigned)S0, 4, 2) &&
+              tsp_sh_ok(a1 + (unsigned)S1, 4, 2) && tsp_sh_ok(a0 + C, 4, 2) &&
+              tsp_sh_ok(a1 + C, 4, 2) && tsp_sh_ok(a0 + C + (unsigned)S0, 4, 2) &&
+              tsp_sh_ok(a1 + C + (unsigned)S1, 4, 2)))
+            return;
+    }
+#endif
     asm volatile(
         "red.shared.add.u32 [%0], %4;\n\tred.shared.add.u32 [%1], %5;\n\t"
         "red.shared.add.u32 [%0+%2], %6;\n\tred.shared.add.u32 [%1+%3], %7;\n\t"
@@ -1173,6 +1197,9 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
     constexpr int kCols = tm_block_cols(LMAX, kWarps);
     if (warp == 0) tm_alloc<kCols>(&s_tmem);
     init_block_sums(&s_sums);
+#ifdef TSP_DEBUG_CHECKS
+    if (tid == 0) tsp_dbg_word = 0ull;
+#endif
     // the slack around the rho' region is read (times P = 0) by the
     // unpredicated pass-1 loads, so it must hold finite values
     if (!BATCH) {
@@ -1200,6 +1227,10 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
             if (cur >= 0 && tid == 0) {
                 flush_block_sums(&s_sums, s_inst.accum, MODE);
                 init_block_sums(&s_sums);
+#ifdef TSP_DEBUG_CHECKS
+                if (tsp_dbg_word) atomicCAS(&s_inst.accum->dbg, 0ull, tsp_dbg_word);
+                tsp_dbg_word = 0ull;
+#endif
             }
             __syncthreads();
             const unsigned long long* src = reinterpret_cast<const unsigned long long*>(table + item.w);
@@ -1285,6 +1316,10 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
     }
     tm_sync_threads();
     if (!BATCH || cur >= 0) flush_block_sums(&s_sums, I.accum, MODE);
+#ifdef TSP_DEBUG_CHECKS
+    if (tid == 0 && tsp_dbg_word && (!BATCH || cur >= 0))
+        atomicCAS(&I.accum->dbg, 0ull, tsp_dbg_word);
+#endif
     if (warp == 0) tm_dealloc<kCols>(s_tmem);
 }
 
