@@ -207,3 +207,29 @@ def test_sharded_loglik_grad_parts_add_up():
     assert L_sh == pytest.approx(L, rel=1e-6)
     assert float(torch.linalg.norm(g_sh - g.double()) / torch.linalg.norm(g.double())) <= 1e-5
     np.testing.assert_allclose(gs_sh, gs, rtol=1e-5)
+
+
+def test_tuned_schedule_cache_and_logged_iterations(tmp_path):
+    """tuning.tuned_schedule on the real library: autotune once, then the
+    cached schedule is applied to a second context; iterate_logged records
+    count conservation and a log-likelihood that does not decrease (EM)."""
+    from paper_1502_07478_gb300.tuning import iterate_logged, tuned_schedule
+    w = make_workload("small_5mm")
+    ev = w.events()
+    path = str(tmp_path / "sched.json")
+    a = _recon(w)
+    a.upload_events(*ev)
+    ra = tuned_schedule(a, path)
+    assert not ra["cached"] and a.schedule() == ra["schedule"]
+    b = _recon(w)
+    b.upload_events(*ev)
+    rb = tuned_schedule(b, path)
+    assert rb["cached"] and b.schedule() == ra["schedule"]
+    recs = iterate_logged(b, 4)
+    assert [r["iteration"] for r in recs] == [1, 2, 3, 4]
+    for r in recs:
+        assert abs(r["conservation_rel"]) < 2e-6
+    ll = [r["loglik"] for r in recs]
+    assert all(y >= x - 1e-9 * abs(x) for x, y in zip(ll, ll[1:]))
+    a.close()
+    b.close()
