@@ -220,11 +220,11 @@ def test_tuned_schedule_cache_and_logged_iterations(tmp_path):
     a = _recon(w)
     a.upload_events(*ev)
     ra = tuned_schedule(a, path)
-    assert not ra["cached"] and a.schedule() == ra["schedule"]
+    assert not ra["cached"] and a.schedule == ra["schedule"]
     b = _recon(w)
     b.upload_events(*ev)
     rb = tuned_schedule(b, path)
-    assert rb["cached"] and b.schedule() == ra["schedule"]
+    assert rb["cached"] and b.schedule == ra["schedule"]
     recs = iterate_logged(b, 4)
     assert [r["iteration"] for r in recs] == [1, 2, 3, 4]
     for r in recs:
