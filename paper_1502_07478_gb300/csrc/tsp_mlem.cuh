@@ -352,12 +352,13 @@ __device__ __forceinline__ void red_add(const RowK<SMEM>& r, int lim, int m, flo
 }
 
 // P cache in tensor memory.  Each thread keeps the kernel values of its row
-// segment in its own TMEM lane instead of registers: warp w uses lanes
-// 32 (w mod 4) .. +31 (the lane quarter a warp may access) and a slice of
-// tm_slice(LMAX) columns starting at column tm_slice(LMAX) * (w / 4).  Pass 1
-// stores four steps at a time, pass 2 loads them back; the registers this
-// frees go to more resident warps.  (The paper's kernel keeps P in registers
-// or recomputes it.)
+// segment (P rho' in the fixed-point MLEM pass) in its own TMEM lane instead of
+// registers: warp w uses lanes 32 (w mod 4) .. +31 (the lane quarter a warp may
+// access) and a slice of tm_slice(LMAX) columns starting at column
+// tm_slice(LMAX) * (w / 4).  Pass 1 stores 16, 8 or 4 values at a time (4 in
+// the scalar pass), pass 2 loads them back; the registers this frees go to
+// more resident warps.  (The paper's kernel keeps P in registers or
+// recomputes it.)
 __host__ __device__ constexpr int pow2_at_least(int x, int p = 1)
 {
     return p >= x ? p : pow2_at_least(x, 2 * p);
