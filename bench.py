@@ -63,13 +63,13 @@ FMA_OPS_PER_PIXEL = 17
 # DRAM bytes per event of one MLEM tile pass (dram__bytes_read.sum +
 # dram__bytes_write.sum of one ncu-captured launch over 1e6 events of the
 # 1 mm workload); the traffic grows with the events.
-TILE_PASS_DRAM_B_PER_EVENT = 47.7
+TILE_PASS_DRAM_B_PER_EVENT = 47.6
 # The same for the accumulator-only tile pass of the 0.5 mm stress workload
 # (one launch over its first 1e6 events; rho' re-read through L1/L2).
 GLD_PASS_DRAM_B_PER_EVENT = 66.0
 # Warp instructions issued per in-window pixel evaluation (smsp__inst_executed.sum
 # / W of the same captures): the pass is issue-bound, so this is its tracked cost.
-TILE_PASS_WARP_INST_PER_EVAL = 1.07
+TILE_PASS_WARP_INST_PER_EVAL = 1.06
 GLD_PASS_WARP_INST_PER_EVAL = 1.17
 
 

@@ -1093,25 +1093,36 @@ __device__ __forceinline__ void event_rows(const Geo& g, const EventsView& evs, 
     }
 }
 
-// NSEG = 1: lane-row q = wig*32 + lane covers its row whole (kAlt).  NSEG = 2:
+// NSEG = 1: lane-row q = blk*32 + lane covers its row whole (kAlt).  NSEG = 2:
 // even warps cover the right halves and odd warps the left halves of rows
-// (wig/2)*32 + lane (a warp-uniform choice, no divergence).
+// rb*32 + lane (a warp-uniform choice, no divergence).  The row block of warp
+// wig is rotated by the group's index (rot = grp mod the number of blocks):
+// a block's warps sit on the SM's schedulers by warp index mod 4, and without
+// the rotation warp wig of every group, with the same rows of the window (the
+// middle rows, with the longest chords, for wig = 0), would land on the same
+// scheduler, which would then carry the most work.
 template <int LMAX, int MODE, int NSEG, bool SMEM, bool GLD, bool KZ>
 __device__ __forceinline__ void process_event(const Geo& g, const EventsView& evs, int e, int G,
                                               int wig, int lane, int bar_id, float* part,
                                               int& parity, const Frame* f, const float* rp_base,
-                                              float* acc_base, BlockSums* bs, unsigned tma)
+                                              float* acc_base, BlockSums* bs, unsigned tma,
+                                              int rot)
 {
     if constexpr (NSEG == 1) {
-        event_rows<kAlt, LMAX, MODE, SMEM, GLD, KZ>(g, evs, e, wig * 32 + lane, f, rp_base, acc_base,
+        int blk = wig + rot;
+        blk -= blk >= G ? G : 0;
+        event_rows<kAlt, LMAX, MODE, SMEM, GLD, KZ>(g, evs, e, blk * 32 + lane, f, rp_base, acc_base,
                                                G, wig, lane, bar_id, part, parity, bs, tma);
     } else {
+        const int nb = G >> 1;
+        int rb = (wig >> 1) + rot;
+        rb -= rb >= nb ? nb : 0;
         if ((wig & 1) == 0)
-            event_rows<kPos, LMAX, MODE, SMEM, GLD, KZ>(g, evs, e, (wig >> 1) * 32 + lane, f,
+            event_rows<kPos, LMAX, MODE, SMEM, GLD, KZ>(g, evs, e, rb * 32 + lane, f,
                                                    rp_base, acc_base, G, wig, lane, bar_id, part,
                                                    parity, bs, tma);
         else
-            event_rows<kNeg, LMAX, MODE, SMEM, GLD, KZ>(g, evs, e, (wig >> 1) * 32 + lane, f,
+            event_rows<kNeg, LMAX, MODE, SMEM, GLD, KZ>(g, evs, e, rb * 32 + lane, f,
                                                    rp_base, acc_base, G, wig, lane, bar_id, part,
                                                    parity, bs, tma);
     }
@@ -1283,11 +1294,13 @@ k_tiles(Inst p, const Inst* __restrict__ table, const int4* __restrict__ items, 
             }
         }
         __syncthreads();
-        if (grp < ngroups)
+        if (grp < ngroups) {
+            const int rot = grp % (NSEG == 1 ? G : (G >> 1));
             for (int e = item.y + grp; e < item.y + item.z; e += ngroups)
                 process_event<LMAX, MODE, NSEG, true, GLD, KZ>(
                     g, I.evs, e, G, wig, lane, 1 + grp, part, parity, &s_frame,
-                    GLD ? I.rhop : s_rp, s_acc, &s_sums, tma);
+                    GLD ? I.rhop : s_rp, s_acc, &s_sums, tma, rot);
+        }
         __syncthreads();
         if (MODE != kLoglik) {
             for (int rr = warp; rr < tl.RH; rr += kWarps) {
@@ -1356,10 +1369,11 @@ k_outliers(Geo g, EventsView evs, int first, int count, const float* __restrict_
     tm_sync_threads();
     const unsigned tma = tm_thread_addr<LMAX>(s_tmem, warp);
     if (grp < ngroups) {
+        const int rot = grp % (NSEG == 1 ? G : (G >> 1));
         for (int k = blockIdx.x * ngroups + grp; k < count; k += gridDim.x * ngroups)
             process_event<LMAX, MODE, NSEG, false, false, true>(g, evs, first + k, G, wig, lane,
                                                                 1 + grp, part, parity, &s_frame,
-                                                                rhop, A, &s_sums, tma);
+                                                                rhop, A, &s_sums, tma, rot);
     }
     tm_sync_threads();
     flush_block_sums(&s_sums, accum, MODE);
@@ -1399,11 +1413,13 @@ k_outliers_batch(const Inst* __restrict__ table, const int4* __restrict__ items,
         const int grp = warp / G, wig = warp - grp * G;
         float* part = s_part + grp * (2 * 3 * G);
         int parity = 0;
-        if (grp < ngroups)
+        if (grp < ngroups) {
+            const int rot = grp % (NSEG == 1 ? G : (G >> 1));
             for (int k = grp; k < item.z; k += ngroups)
                 process_event<LMAX, MODE, NSEG, false, false, true>(
                     s_inst.g, s_inst.evs, item.y + k, G, wig, lane, 1 + grp, part, parity,
-                    &s_frame, s_inst.rhop, s_inst.A, &s_sums, tma);
+                    &s_frame, s_inst.rhop, s_inst.A, &s_sums, tma, rot);
+        }
         __syncthreads();
         flush_block_sums(&s_sums, s_inst.accum, MODE);
     }
