@@ -70,7 +70,7 @@ GLD_PASS_DRAM_B_PER_EVENT = 66.0
 # Warp instructions issued per in-window pixel evaluation (smsp__inst_executed.sum
 # / W of the same captures): the pass is issue-bound, so this is its tracked cost.
 TILE_PASS_WARP_INST_PER_EVAL = 1.06
-GLD_PASS_WARP_INST_PER_EVAL = 1.17
+GLD_PASS_WARP_INST_PER_EVAL = 1.16
 
 
 def roofline_basis(device: int):
