@@ -56,7 +56,7 @@ def _bound(w, ey, t):
 
 def test_q_bound_below_window_minimum():
     for name, n in (("small_5mm", 400), ("paper_1mm", 60)):
-        w = make_workload(name)
+        w = make_workload(name, n_events=n)
         ey, ez, t = _events(w, n)
         for j in range(n):
             qmin = _q_min_over_window(w, ey[j], ez[j], t[j])
